@@ -1,0 +1,239 @@
+/*
+ * lp.h -- C ABI of the GB300 (sm_103a) sketch-preconditioned interior-point LP solver.
+ *
+ * Method: Chowdhury, London, Avron & Drineas, "Speeding up Linear Programming
+ * using Randomized Linear Algebra" (arXiv 2003.08072).  The library solves
+ * standard-form LPs  min c^T x  s.t.  A x = b, x >= 0  (Sec. 1, primal and
+ * dual problems) with m << n by the infeasible long-step IPM of Algorithm 2,
+ * whose normal equations A D^2 A^T dy = p (Eq. normal) are solved by the
+ * sketch-preconditioned CG of Algorithm 1 plus the correction vector v of
+ * Eq. compv.
+ *
+ * Conventions for every entry point
+ *   - Return value: an lp_status; LP_OK on success.  No entry point aborts or
+ *     throws.  lp_last_error() returns a message for the calling thread's
+ *     most recent failure.
+ *   - Dense matrices are column-major unless the layout says otherwise.
+ *     Vectors are float64.  Indices are 0-based.
+ *   - "device" pointers must be CUDA device (or managed) memory on the
+ *     context's device; "host or device" pointers are classified with
+ *     cudaPointerGetAttributes.  The caller owns every buffer it passes and
+ *     keeps it alive until the call returns (synchronous entry points) or
+ *     until the stream passes the enqueued work (entry points marked
+ *     "asynchronous").
+ *   - All device work of a context is enqueued on the stream given to
+ *     lp_create (NULL = the legacy default stream).  A context must not be
+ *     used from two threads at once.
+ */
+#ifndef LP_GB300_H
+#define LP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lp_ctx lp_ctx;
+
+typedef enum {
+  LP_OK = 0,
+  LP_ERR_ARG = 1,            /* bad argument: size, NULL, NaN/Inf input, unsupported combination */
+  LP_ERR_OOM = 2,            /* device allocation failed */
+  LP_ERR_CUDA = 3,           /* a CUDA runtime call failed (message in lp_last_error) */
+  LP_ERR_BREAKDOWN = 4,      /* factorization of the sketch met a non-positive pivot (rank(ADW) < m) */
+  LP_ERR_NOT_CONVERGED = 5,  /* iteration cap reached; outputs hold the last iterate */
+  LP_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  LP_ERR_NUMERIC = 7         /* NaN/Inf appeared in the iteration */
+} lp_status;
+
+typedef enum {
+  LP_DENSE_COLMAJOR = 0,     /* A_vals is m x n, element (i, j) at i + j*m */
+  LP_DENSE_ROWMAJOR = 1,     /* A_vals is m x n, element (i, j) at i*n + j */
+  LP_CSR = 2                 /* indptr (m+1, int64), indices (nnz, int32 column ids), A_vals (nnz) */
+} lp_layout;
+
+typedef enum { LP_F64 = 0, LP_F32 = 1, LP_BF16 = 2, LP_F16 = 3 } lp_dtype;
+
+/* Parameters of Algorithms 1 and 2.  Defaults from lp_params_default(). */
+typedef struct {
+  double tol;            /* stop when ||r_p||/(1+||b||), ||r_d||/(1+||c||), n mu/(1+|c^T x|) <= tol (1e-8) */
+  double cg_rel_tol;     /* CG stops when ||f^(j)|| <= cg_rel_tol ||f^(0)|| (1e-6), Sec. 6 "tolCG" */
+  double sigma;          /* centering parameter in (0, 4/5), Alg. 2 input (0.5, Sec. 6) */
+  double gamma;          /* neighbourhood N(gamma) width in (0, 1), Sec. 4 (0.99) */
+  int32_t cg_max_iter;   /* CG iteration cap per solve (500) */
+  int32_t ipm_max_iter;  /* IPM iteration cap (200) */
+  int32_t refine_max;    /* FP64 refinement steps for Q^{-1} r~ and for a low-precision dy (6) */
+  int32_t sketch_s;      /* nonzeros per row of W: 1 = CountSketch, 4 = sparse sign (4) */
+  int32_t sketch_w;      /* sketch width w; 0 = 4m.  Must be a multiple of sketch_s */
+  int32_t cg_theory_rule;/* 1: CG also stops only once ||f|| <= gamma sigma sqrt(mu)/(4 sqrt(n)) (Sec. 4) (1) */
+  uint64_t seed;         /* W for IPM iteration k is a function of (seed, k) only (0) */
+  lp_dtype stream_dtype; /* dtype A is streamed in by the CG matvec; LP_F64 keeps the input dtype (LP_F64) */
+  int32_t cg_batch;      /* CG iterations enqueued between host checks of the stop flag (4) */
+} lp_params;
+
+/* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */
+typedef struct {
+  int32_t ipm_iters;       /* outer iterations taken */
+  int32_t cg_iters_total;  /* products with A D^2 A^T over all CG solves */
+  int32_t cg_iters_last;   /* CG iterations of the last normal-equation solve */
+  int32_t refine_steps;    /* FP64 refinement steps of the last solve */
+  double rp_rel, rd_rel, gap_rel;   /* scaled residuals of the stopping rule at exit */
+  double mu;               /* duality measure x^T s / n at exit */
+  double obj;              /* c^T x at exit */
+  double alpha_max, alpha; /* step-length quantities of the last iteration (Alg. 2 (e), (f)) */
+  double f_norm;           /* ||f^(t)|| of the last CG solve (Sec. 3) */
+  double v_norm;           /* ||v|| of the last correction vector (Eq. compv) */
+  int32_t status;          /* lp_status of the solve */
+} lp_info;
+
+/* Fills *prm with the defaults listed above.  LP_ERR_ARG if prm is NULL. */
+lp_status lp_params_default(lp_params* prm);
+
+/* Human-readable name of a status code (static string). */
+const char* lp_status_str(lp_status st);
+
+/* Message describing the calling thread's most recent error ("" if none). */
+const char* lp_last_error(void);
+
+/*
+ * lp_create -- copy an LP instance (Eq. primal: A, b, c) to the device.
+ *   out      : receives the new context (set to NULL on failure).
+ *   m, n     : constraint and variable counts, 1 <= m <= n, m <= 8192.
+ *   layout   : LP_DENSE_COLMAJOR / LP_DENSE_ROWMAJOR / LP_CSR.
+ *   a_dtype  : element type of A_vals: LP_F64 or LP_F32 (dense); LP_F32 or LP_F64 (CSR).
+ *   A_vals   : host or device; dense m*n elements, or nnz CSR values.
+ *   indptr   : CSR only (m+1 int64, host or device); NULL for dense.
+ *   indices  : CSR only (nnz int32 column ids, host or device); NULL for dense.
+ *   nnz      : CSR only; 0 for dense.
+ *   b, c     : host or device, m and n float64.
+ *   prm      : parameters (copied); NULL = defaults.
+ *   stream   : cudaStream_t all work is enqueued on (NULL = legacy default).
+ * The context owns all device memory it allocates: the matrix in the layout
+ * the kernels stream (column-major with 16-byte aligned columns, or CSC),
+ * a low-precision copy when prm->stream_dtype asks for one, and the
+ * workspaces.  Errors: LP_ERR_ARG (sizes, NULL, non-finite entries, dtype),
+ * LP_ERR_OOM, LP_ERR_CUDA.  Synchronous.
+ */
+lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout layout, lp_dtype a_dtype,
+                    const void* A_vals, const int64_t* indptr, const int32_t* indices, int64_t nnz,
+                    const double* b, const double* c, const lp_params* prm, void* stream);
+
+/* Frees every device buffer of the context.  NULL is a no-op. */
+void lp_destroy(lp_ctx* ctx);
+
+/* Replaces the context's parameters (takes effect on the next call). */
+lp_status lp_set_params(lp_ctx* ctx, const lp_params* prm);
+
+/*
+ * lp_ipm_solve -- Algorithm 2 end to end (Sec. 4).
+ *   x, y, s : host or device, n, m, n float64.  On entry the starting point
+ *             when start_given != 0, else ignored and the start is x = s = 1,
+ *             y = 0 (Sec. 6 starts from all ones).  On exit the last iterate.
+ *   info    : may be NULL.
+ * Per iteration k: residuals and p (Eq. pdef), W = W(seed, k) (step (a)),
+ * Algorithm 1 for dy, v from Eq. compv, ds from Eq. delshat, dx from
+ * Eq. delxhat, alpha_max / alpha (steps (e), (f)), update (step (g)).
+ * Returns LP_OK when the scaled stopping rule holds, LP_ERR_NOT_CONVERGED at
+ * the iteration cap, LP_ERR_BREAKDOWN / LP_ERR_NUMERIC on failure (with the
+ * last finite iterate in x, y, s).  Synchronous.
+ */
+lp_status lp_ipm_solve(lp_ctx* ctx, double* x, double* y, double* s, int32_t start_given,
+                       lp_info* info);
+
+/*
+ * lp_normal_solve -- Algorithm 1 plus the correction of Eq. compv for one iterate.
+ *   x, s    : device, n float64, strictly positive; D^2 = X S^{-1} (Sec. 1).
+ *   p       : device, m float64 right-hand side.
+ *   k       : IPM iteration index selecting W = W(seed, k) (Alg. 2 step (a)).
+ *   dy      : device, m float64 output: the CG solution dy-hat = Q^{-1/2} z^t.
+ *   rtil    : device, m float64 output or NULL: r~ = A D^2 A^T dy - p (FP64).
+ *   u       : device, w float64 output or NULL: u = (A D W)^dagger r~.
+ *   Wu      : device, n float64 output or NULL: W u, so that S^{-1} v = D W u.
+ *   Atdy    : device, n float64 output or NULL: A^T dy (FP64).
+ *   info    : may be NULL; receives cg_iters_last, refine_steps, f_norm.
+ * Errors: LP_ERR_ARG, LP_ERR_BREAKDOWN (rank-deficient sketch), LP_ERR_NUMERIC,
+ * LP_ERR_CUDA.  Synchronous.
+ */
+lp_status lp_normal_solve(lp_ctx* ctx, const double* x, const double* s, const double* p,
+                          int32_t k, double* dy, double* rtil, double* u, double* Wu,
+                          double* Atdy, lp_info* info);
+
+/* ---------------- row-level entry points (one step of the hot path each) ---------------- */
+
+/*
+ * lp_residuals -- Alg. 2 step (b) in one pass over A:
+ *   r_p = A x - b, r_d = A^T y + s - c, mu = x^T s / n (Eq. update) and
+ *   p = -r_p - sigma mu A S^{-1} 1 + A x - A D^2 r_d (Eq. pdef), computed as
+ *   p = b - A(sigma mu / s + d^2 r_d).
+ *   x, y, s : device (n, m, n).  rp, p: device m outputs.  rd: device n output.
+ *   mu_out  : host double output (may be NULL).  Synchronous.
+ */
+lp_status lp_residuals(lp_ctx* ctx, const double* x, const double* y, const double* s,
+                       double sigma, double* rp, double* rd, double* p, double* mu_out);
+
+/*
+ * lp_sketch_indices -- the buckets and signs of W for iteration k (Sec. 2, Eq. pdprec):
+ *   key = SplitMix64(seed ^ SplitMix64(k)); h = SplitMix64(key ^ (i*s + j));
+ *   bucket = j*(w/s) + (((h >> 32) * (w/s)) >> 32); sign = (h & 1) ? -1 : +1.
+ *   bucket : device int32 output, n*s (row i, nonzero j at i*s + j).
+ *   sign   : device int8 output, n*s (+1 / -1).
+ *   stream : cudaStream_t.  Asynchronous.  LP_ERR_ARG if w % s != 0 or sizes invalid.
+ */
+lp_status lp_sketch_indices(uint64_t seed, int32_t k, int64_t n, int32_t s, int32_t w,
+                            int32_t* bucket, int8_t* sign, void* stream);
+
+/*
+ * lp_sketch -- A D W (m x w, Eq. pdprecond; Alg. 1 step 1) for W = W(seed, k).
+ *   d  : device n float64, the diagonal of D = (X S^{-1})^{1/2}.
+ *   G  : device m*w float64 output, column-major (leading dimension m).
+ * FP64 accumulation from the input-precision A.  Synchronous.
+ */
+lp_status lp_sketch(lp_ctx* ctx, const double* d, int32_t k, double* G);
+
+/*
+ * lp_factor -- preconditioner of Alg. 1 step 2 from the sketch G = A D W:
+ *   Q = G G^T (Eq. pdprecond) and Minv = Q^{-1}, so that PCG with M = Q gives the
+ *   iterates of CG on Eq. precond_alt.
+ *   G    : device m*w float64, column-major.
+ *   Q    : device m*m float64 output or NULL (symmetric).
+ *   Minv : device m*m float64 output or NULL (symmetric).
+ * LP_ERR_BREAKDOWN if a pivot is not positive (rank(G) < m).  Synchronous.
+ */
+lp_status lp_factor(lp_ctx* ctx, const double* G, double* Q, double* Minv);
+
+/*
+ * lp_normal_matvec -- y = A D^2 A^T v (the operator of Eq. normal), one pass over A.
+ *   d2     : device n float64 (D^2).  v: device m float64.  y: device m float64 output.
+ *   t      : device n float64 output or NULL: t = A^T v.
+ *   stream_dtype : LP_F64 = input precision with FP64 accumulation; LP_F32 /
+ *            LP_BF16 / LP_F16 = the context's streamed copy with FP32 accumulation
+ *            (must match the context's stream_dtype unless LP_F64).
+ * Synchronous.
+ */
+lp_status lp_normal_matvec(lp_ctx* ctx, const double* d2, const double* v, double* y, double* t,
+                           lp_dtype stream_dtype);
+
+/*
+ * lp_step -- Alg. 2 steps (d)-(g) for a given dy (fused IPM update, Sec. 4):
+ *   ds = -r_d - A^T dy (Eq. delshat); S^{-1} v = D (W u) (Eq. compv);
+ *   dx = -x + sigma mu S^{-1} 1 - D^2 ds - S^{-1} v (Eq. delxhat);
+ *   alpha_max keeps [0, alpha] inside N(gamma) (step (e)); alpha minimises
+ *   mu(alpha) on [0, alpha_max] (step (f)); then x += alpha dx, y += alpha dy,
+ *   s += alpha ds (step (g)).
+ *   x, y, s : device, updated in place.   rd, Atdy, Wu: device n float64.
+ *   dy      : device m.   mu: current x^T s / n.   eta = ||r||/||r^0||.  mu0 = x0^T s0 / n.
+ *   dx, ds  : device n float64 outputs or NULL (the directions).
+ *   out     : host double[4] output or NULL: {alpha_max, alpha, x^T ds + s^T dx, dx^T ds}.
+ * Synchronous.
+ */
+lp_status lp_step(lp_ctx* ctx, double* x, double* y, double* s, const double* rd,
+                  const double* dy, const double* Atdy, const double* Wu, double mu, double eta,
+                  double mu0, double* dx, double* ds, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP_GB300_H */

@@ -1,0 +1,212 @@
+"""ctypes binding of the C ABI in include/lp.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and forwards plain pointers
+and sizes; all arithmetic runs in the CUDA library.  Pointers may be given as integers, as
+torch tensors (``data_ptr()``) or as numpy arrays (host memory).  A non-OK status raises
+``LPError`` carrying the status and the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+from . import build as _build
+
+LP_OK, LP_ERR_ARG, LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_BREAKDOWN = 0, 1, 2, 3, 4
+LP_ERR_NOT_CONVERGED, LP_ERR_TIMEOUT, LP_ERR_NUMERIC = 5, 6, 7
+LP_DENSE_COLMAJOR, LP_DENSE_ROWMAJOR, LP_CSR = 0, 1, 2
+LP_F64, LP_F32, LP_BF16, LP_F16 = 0, 1, 2, 3
+
+DTYPE_CODES = {"f64": LP_F64, "f32": LP_F32, "bf16": LP_BF16, "f16": LP_F16}
+
+
+class lp_params(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("cg_rel_tol", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("cg_max_iter", ctypes.c_int32),
+        ("ipm_max_iter", ctypes.c_int32),
+        ("refine_max", ctypes.c_int32),
+        ("sketch_s", ctypes.c_int32),
+        ("sketch_w", ctypes.c_int32),
+        ("cg_theory_rule", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("stream_dtype", ctypes.c_int),
+        ("cg_batch", ctypes.c_int32),
+    ]
+
+
+class lp_info(ctypes.Structure):
+    _fields_ = [
+        ("ipm_iters", ctypes.c_int32),
+        ("cg_iters_total", ctypes.c_int32),
+        ("cg_iters_last", ctypes.c_int32),
+        ("refine_steps", ctypes.c_int32),
+        ("rp_rel", ctypes.c_double),
+        ("rd_rel", ctypes.c_double),
+        ("gap_rel", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("obj", ctypes.c_double),
+        ("alpha_max", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("f_norm", ctypes.c_double),
+        ("v_norm", ctypes.c_double),
+        ("status", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_str(status)}: {msg}")
+        self.status = status
+
+
+_LIB: Optional[ctypes.CDLL] = None
+_VP = ctypes.c_void_p
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+_SIGNATURES = {
+    "lp_params_default": (ctypes.c_int, [ctypes.POINTER(lp_params)]),
+    "lp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "lp_last_error": (ctypes.c_char_p, []),
+    "lp_create": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _I64, ctypes.c_int, ctypes.c_int, _VP,
+                                 _VP, _VP, _I64, _VP, _VP, ctypes.POINTER(lp_params), _VP]),
+    "lp_destroy": (None, [_VP]),
+    "lp_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(lp_params)]),
+    "lp_ipm_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, ctypes.POINTER(lp_info)]),
+    "lp_normal_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP,
+                                       ctypes.POINTER(lp_info)]),
+    "lp_residuals": (ctypes.c_int, [_VP, _VP, _VP, _VP, _D, _VP, _VP, _VP, ctypes.POINTER(_D)]),
+    "lp_sketch_indices": (ctypes.c_int, [ctypes.c_uint64, _I32, _I64, _I32, _I32, _VP, _VP, _VP]),
+    "lp_sketch": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
+    "lp_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "lp_normal_matvec": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "lp_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _D, _D, _D, _VP, _VP,
+                               _VP]),
+}
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads (building first if needed) the CUDA library; raises if it cannot."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {path} is missing: run the build first")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _p(x) -> Optional[int]:
+    """Pointer of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _check(st: int):
+    if st != LP_OK:
+        raise LPError(st, last_error())
+
+
+def status_str(st: int) -> str:
+    return load().lp_status_str(st).decode()
+
+
+def last_error() -> str:
+    return load().lp_last_error().decode()
+
+
+def lp_params_default() -> lp_params:
+    p = lp_params()
+    _check(load().lp_params_default(ctypes.byref(p)))
+    return p
+
+
+def lp_create(m, n, layout, a_dtype, A_vals, indptr, indices, nnz, b, c, params=None,
+              stream=None) -> int:
+    ctx = _VP()
+    prm = params if params is not None else lp_params_default()
+    _check(load().lp_create(ctypes.byref(ctx), m, n, layout, a_dtype, _p(A_vals), _p(indptr),
+                            _p(indices), nnz, _p(b), _p(c), ctypes.byref(prm), _p(stream)))
+    return ctx.value
+
+
+def lp_destroy(ctx: int):
+    if ctx:
+        load().lp_destroy(ctx)
+
+
+def lp_set_params(ctx, params: lp_params):
+    _check(load().lp_set_params(ctx, ctypes.byref(params)))
+
+
+def lp_ipm_solve(ctx, x, y, s, start_given=False, check=True) -> lp_info:
+    info = lp_info()
+    st = load().lp_ipm_solve(ctx, _p(x), _p(y), _p(s), 1 if start_given else 0, ctypes.byref(info))
+    if check and st not in (LP_OK,):
+        raise LPError(st, last_error())
+    return info
+
+
+def lp_normal_solve(ctx, x, s, p, k, dy, rtil=None, u=None, Wu=None, Atdy=None) -> lp_info:
+    info = lp_info()
+    _check(load().lp_normal_solve(ctx, _p(x), _p(s), _p(p), k, _p(dy), _p(rtil), _p(u), _p(Wu),
+                                  _p(Atdy), ctypes.byref(info)))
+    return info
+
+
+def lp_residuals(ctx, x, y, s, sigma, rp, rd, p) -> float:
+    mu = _D()
+    _check(load().lp_residuals(ctx, _p(x), _p(y), _p(s), sigma, _p(rp), _p(rd), _p(p),
+                               ctypes.byref(mu)))
+    return mu.value
+
+
+def lp_sketch_indices(seed, k, n, s, w, bucket, sign, stream=None):
+    _check(load().lp_sketch_indices(seed, k, n, s, w, _p(bucket), _p(sign), _p(stream)))
+
+
+def lp_sketch(ctx, d, k, G):
+    _check(load().lp_sketch(ctx, _p(d), k, _p(G)))
+
+
+def lp_factor(ctx, G, Q=None, Minv=None):
+    _check(load().lp_factor(ctx, _p(G), _p(Q), _p(Minv)))
+
+
+def lp_normal_matvec(ctx, d2, v, y, t=None, stream_dtype=LP_F64):
+    _check(load().lp_normal_matvec(ctx, _p(d2), _p(v), _p(y), _p(t), stream_dtype))
+
+
+def lp_step(ctx, x, y, s, rd, dy, Atdy, Wu, mu, eta, mu0, dx=None, ds=None):
+    out = (ctypes.c_double * 4)()
+    _check(load().lp_step(ctx, _p(x), _p(y), _p(s), _p(rd), _p(dy), _p(Atdy), _p(Wu), mu, eta,
+                          mu0, _p(dx), _p(ds), ctypes.cast(out, _VP)))
+    return tuple(out)

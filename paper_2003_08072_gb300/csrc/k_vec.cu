@@ -1,0 +1,431 @@
+// Vector kernels: reduction of per-CTA partials, CG scalar steps, preconditioner apply,
+// and the fused IPM update (Alg. 2 steps (d)-(g)).  All vectors and scalars are FP64.
+#include <math.h>
+
+#include "dev_util.cuh"
+
+namespace lpk {
+
+// ------------------------------------------------------------------------------------
+// Partials [nblk][nout][m] -> m-vectors.  32 rows x 8 block groups per CTA.
+// ------------------------------------------------------------------------------------
+template <typename ACC>
+__global__ void __launch_bounds__(256) k_reduce(RedArgs a) {
+  if (a.skip_if_done && a.fl[FL_DONE]) return;
+  __shared__ double sh[2][8][33];
+  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int row = blockIdx.x * 32 + rl;
+  const ACC* part = reinterpret_cast<const ACC*>(a.part);
+  double s0 = 0.0, s1 = 0.0;
+  if (row < a.m) {
+    for (int b = g; b < a.nblk; b += 8) {
+      s0 += (double)part[((size_t)b * a.nout) * a.m + row];
+      if (a.nout > 1) s1 += (double)part[((size_t)b * a.nout + 1) * a.m + row];
+    }
+  }
+  sh[0][g][rl] = s0;
+  sh[1][g][rl] = s1;
+  __syncthreads();
+  double contrib[2] = {0.0, 0.0};
+  if (g == 0) {
+    double t0 = 0.0, t1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      t0 += sh[0][k][rl];
+      t1 += sh[1][k][rl];
+    }
+    if (row < a.m) {
+      switch (a.mode) {
+        case RED_PLAIN: a.out0[row] = t0; break;
+        case RED_MINUS_P: a.out0[row] = t0 - a.p0[row]; break;
+        case RED_RESID: {
+          const double rp = t0 - a.p0[row];
+          a.out0[row] = rp;
+          a.out1[row] = a.p0[row] - t1;
+          contrib[0] = rp * rp;
+          break;
+        }
+        case RED_CG_Q: {
+          a.out0[row] = t0;
+          contrib[0] = a.dvec[row] * t0;
+          break;
+        }
+      }
+    }
+  }
+  if (a.mode == RED_RESID || a.mode == RED_CG_Q) {
+    double v[1] = {contrib[0]};
+    if (grid_sum_last<1>(v, a.bpart, a.bcnt) && threadIdx.x == 0) {
+      if (a.mode == RED_RESID) {
+        a.sc[SC_RP2] = v[0];
+      } else {
+        const double dq = v[0];
+        a.sc[SC_DQ] = dq;
+        if (!(dq > 0.0) || !isfinite(dq)) {
+          a.fl[FL_NUMERIC] = 1;
+          a.fl[FL_DONE] = 1;
+          a.sc[SC_ALPHA] = 0.0;
+        } else {
+          a.sc[SC_ALPHA] = a.sc[SC_RHO] / dq;
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st) {
+  const int grid = (a.m + 31) / 32;
+  if (a.acc_f64)
+    k_reduce<double><<<grid, 256, 0, st>>>(a);
+  else
+    k_reduce<float><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Iterate preparation: d2 = x/s, d = sqrt(d2); x^T s, c^T x -> mu, sigma mu.
+// ------------------------------------------------------------------------------------
+__global__ void k_prep(const double* __restrict__ x, const double* __restrict__ s, int64_t n,
+                       double* __restrict__ d2, double* __restrict__ d, double* sc, double* bpart,
+                       unsigned* bcnt, double sigma, const double* __restrict__ c) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double xi = x[i], si = s[i];
+    const double q = xi / si;
+    d2[i] = q;
+    d[i] = sqrt(q);
+    v[0] += xi * si;
+    v[1] += c[i] * xi;
+  }
+  if (grid_sum_last<2>(v, bpart, bcnt) && threadIdx.x == 0) {
+    sc[SC_XS] = v[0];
+    sc[SC_MU] = v[0] / (double)n;
+    sc[SC_SIGMU] = sigma * v[0] / (double)n;
+    sc[SC_CX] = v[1];
+  }
+}
+
+static int vec_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 1024) g = 1024;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
+                                double* sc, double* bpart, unsigned* bcnt, double sigma,
+                                const double* c, cudaStream_t st) {
+  k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c);
+  return cudaGetLastError();
+}
+
+__global__ void k_norm2(const double* __restrict__ v, int64_t n, double* sc, int slot,
+                        double* bpart, unsigned* bcnt) {
+  double a[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[0] += v[i] * v[i];
+  if (grid_sum_last<1>(a, bpart, bcnt) && threadIdx.x == 0) sc[slot] = a[0];
+}
+
+cudaError_t launch_norm2(const double* v, int64_t n, double* sc, int slot, double* bpart,
+                         unsigned* bcnt, cudaStream_t st) {
+  k_norm2<<<vec_grid(n), 256, 0, st>>>(v, n, sc, slot, bpart, bcnt);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Preconditioner apply z = M r (M = Q^{-1}, full symmetric, row-major, leading dim mp),
+// warp per row, r staged in shared memory; fused r^T z with CG bookkeeping.
+// ------------------------------------------------------------------------------------
+struct SymvArgs {
+  const double* M;
+  int mp, m;
+  const double* r;
+  double* z;
+  double* sc;
+  int* fl;
+  double* bpart;
+  unsigned* bcnt;
+  int mode;
+  double rel2;     // CG relative tolerance squared (CG_INIT)
+};
+
+__global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
+  if (a.mode == SYMV_CG_STEP && a.fl[FL_DONE]) return;
+  extern __shared__ double rs[];
+  for (int i = threadIdx.x; i < a.m; i += blockDim.x) rs[i] = a.r[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * 8 + warp;
+  double dotc = 0.0;
+  if (row < a.m) {
+    const double* Mr = a.M + (size_t)row * a.mp;
+    double acc = 0.0;
+    for (int j = lane; j < a.m; j += 32) acc = fma(Mr[j], rs[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      a.z[row] = acc;
+      dotc = acc * rs[row];
+    }
+  }
+  if (a.mode == SYMV_PLAIN) return;
+  double v[1] = {dotc};
+  if (!grid_sum_last<1>(v, a.bpart, a.bcnt) || threadIdx.x != 0) return;
+  const double rho = v[0];
+  if (a.mode == SYMV_F2) {
+    a.sc[SC_F2] = rho;
+    return;
+  }
+  if (!isfinite(rho)) {
+    a.fl[FL_NUMERIC] = 1;
+    a.fl[FL_DONE] = 1;
+    return;
+  }
+  if (a.mode == SYMV_CG_INIT) {
+    a.sc[SC_RHO] = rho;
+    a.sc[SC_RHO0] = rho;
+    const double rel = a.rel2 * rho;
+    const double thr = a.sc[SC_THR2] < rel ? a.sc[SC_THR2] : rel;
+    a.sc[SC_THR2] = thr;
+    a.sc[SC_BETA] = 0.0;
+    a.fl[FL_ITERS] = 0;
+    a.fl[FL_DONE] = (rho <= thr || rho <= 0.0) ? 1 : 0;
+  } else {
+    const int it = a.fl[FL_ITERS] + 1;
+    a.fl[FL_ITERS] = it;
+    a.sc[SC_BETA] = rho / a.sc[SC_RHO];
+    a.sc[SC_RHO] = rho;
+    if (rho <= a.sc[SC_THR2] || it >= a.fl[FL_MAXIT]) a.fl[FL_DONE] = 1;
+  }
+}
+
+cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, double* z,
+                            double* sc, int* fl, double* bpart, unsigned* bcnt, int mode,
+                            cudaStream_t st) {
+  SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, mode, 0.0};
+  const size_t smem = (size_t)m * sizeof(double);
+  k_symv<<<(m + 7) / 8, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, double* z,
+                             double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
+                             cudaStream_t st) {
+  SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, SYMV_CG_INIT, rel_tol * rel_tol};
+  const size_t smem = (size_t)m * sizeof(double);
+  k_symv<<<(m + 7) / 8, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t symv_set_smem(int m) {
+  const int bytes = m * (int)sizeof(double);
+  if (bytes > 48 * 1024)
+    return cudaFuncSetAttribute(k_symv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------
+// CG vector updates
+// ------------------------------------------------------------------------------------
+__global__ void k_cg_axpy(double* dy, double* r, const double* d, const double* q, int m,
+                          const double* sc, const int* fl) {
+  if (fl[FL_DONE]) return;
+  const double al = sc[SC_ALPHA];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    dy[i] = fma(al, d[i], dy[i]);
+    r[i] = fma(-al, q[i], r[i]);
+  }
+}
+
+cudaError_t launch_cg_axpy(double* dy, double* r, const double* d, const double* q, int m,
+                           const double* sc, const int* fl, cudaStream_t st) {
+  k_cg_axpy<<<(m + 255) / 256, 256, 0, st>>>(dy, r, d, q, m, sc, fl);
+  return cudaGetLastError();
+}
+
+__global__ void k_cg_dir(double* d, const double* z, int m, const double* sc, const int* fl) {
+  if (fl[FL_DONE]) return;
+  const double be = sc[SC_BETA];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    d[i] = fma(be, d[i], z[i]);
+}
+
+cudaError_t launch_cg_dir(double* d, const double* z, int m, const double* sc, const int* fl,
+                          cudaStream_t st) {
+  k_cg_dir<<<(m + 255) / 256, 256, 0, st>>>(d, z, m, sc, fl);
+  return cudaGetLastError();
+}
+
+__global__ void k_vec_ops(int op, double* a, const double* b, const double* c, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    switch (op) {
+      case VOP_COPY: a[i] = b[i]; break;
+      case VOP_ZERO: a[i] = 0.0; break;
+      case VOP_ADD: a[i] = b[i] + c[i]; break;
+      case VOP_SUB: a[i] = b[i] - c[i]; break;
+      case VOP_NEG: a[i] = -b[i]; break;
+    }
+  }
+}
+
+cudaError_t launch_vec_ops(int op, double* a, const double* b, const double* c, int m,
+                           const double* sc, cudaStream_t st) {
+  (void)sc;
+  k_vec_ops<<<vec_grid(m), 256, 0, st>>>(op, a, b, c, m);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// IPM update, Alg. 2 step (d): directions and their inner products.
+//   ds = -r_d - A^T dy                            (Eq. delshat)
+//   (W u)_i = sum_j sign_ij / sqrt(s) u[bucket_ij] (gather; W from the same hash as the sketch)
+//   S^{-1} v = D (W u), v = (X S)^{1/2} W u        (Eq. compv)
+//   dx = -x + sigma mu / s - D^2 ds - S^{-1} v     (Eq. delxhat)
+// Sums: x^T ds + s^T dx, dx^T ds, ||v||^2, 1^T v.
+// ------------------------------------------------------------------------------------
+__global__ void k_update_dirs(const double* __restrict__ x, const double* __restrict__ s,
+                              const double* __restrict__ d2, const double* __restrict__ d,
+                              const double* __restrict__ rd, const double* __restrict__ t,
+                              const int32_t* __restrict__ hb, int ss, const double* __restrict__ u,
+                              int64_t n, double* wu, double* dx, double* ds, int wu_given,
+                              double* sc, double* bpart, unsigned* bcnt) {
+  const double sigmu = sc[SC_SIGMU];
+  const double inv_sqrt_s = 1.0 / sqrt((double)ss);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double w;
+    if (wu_given) {
+      w = wu[i];
+    } else {
+      w = 0.0;
+      for (int j = 0; j < ss; ++j) {
+        const int32_t h = hb[i * ss + j];
+        const double uv = u[h & 0x7fffffff];
+        w += (h < 0) ? -uv : uv;
+      }
+      w *= inv_sqrt_s;
+      if (wu) wu[i] = w;
+    }
+    const double xi = x[i], si = s[i];
+    const double dsi = -rd[i] - t[i];
+    const double dxi = -xi + sigmu / si - d2[i] * dsi - d[i] * w;
+    const double vi = sqrt(xi * si) * w;
+    dx[i] = dxi;
+    ds[i] = dsi;
+    acc[0] += xi * dsi + si * dxi;
+    acc[1] += dxi * dsi;
+    acc[2] += vi * vi;
+    acc[3] += vi;
+  }
+  if (grid_sum_last<4>(acc, bpart, bcnt) && threadIdx.x == 0) {
+    sc[SC_B] = acc[0];
+    sc[SC_C] = acc[1];
+    sc[SC_V2] = acc[2];
+    sc[SC_V1] = acc[3];
+  }
+}
+
+cudaError_t launch_update_dirs(const double* x, const double* s, const double* d2, const double* d,
+                               const double* rd, const double* t, const int32_t* hb, int ss,
+                               const double* u, int64_t n, double* wu, double* dx, double* ds,
+                               int wu_given, double* sc, double* bpart, unsigned* bcnt,
+                               cudaStream_t st) {
+  k_update_dirs<<<vec_grid(n), 256, 0, st>>>(x, s, d2, d, rd, t, hb, ss, u, n, wu, dx, ds,
+                                             wu_given, sc, bpart, bcnt);
+  return cudaGetLastError();
+}
+
+// Smallest a in (0, 1] at which a0 + a1 a + a2 a^2 (a0 >= 0) turns negative; +inf if none.
+// Roots from the cancellation-free form of the quadratic formula; a root counts only where
+// the polynomial is decreasing.
+__device__ double first_crossing(double a0, double a1, double a2) {
+  a0 = fmax(a0, 0.0);
+  if (a2 == 0.0) return (a1 < 0.0) ? a0 / (-a1) : INFINITY;
+  const double disc = a1 * a1 - 4.0 * a2 * a0;
+  if (disc < 0.0) return INFINITY;
+  const double sq = sqrt(disc);
+  const double qq = -0.5 * (a1 + (a1 >= 0.0 ? sq : -sq));
+  double best = INFINITY;
+  const double r1 = qq / a2;
+  const double r2 = (qq != 0.0) ? a0 / qq : INFINITY;
+  if (isfinite(r1) && r1 > 0.0 && 2.0 * a2 * r1 + a1 < 0.0) best = fmin(best, r1);
+  if (isfinite(r2) && r2 > 0.0 && 2.0 * a2 * r2 + a1 < 0.0) best = fmin(best, r2);
+  return best;
+}
+
+// Alg. 2 steps (e)-(f).  N(gamma): x_i s_i >= (1-gamma) mu and ||r||/||r0|| <= mu/mu0, with
+// mu(a) = (x^T s + a B + a^2 C)/n and r(a) = (1 - a) r (Eq. iip_3).  alpha_max = first
+// crossing over all conditions (capped at 1); alpha minimises mu(a) on [0, alpha_max],
+// ties to the larger a.
+__global__ void k_step_length(const double* __restrict__ x, const double* __restrict__ s,
+                              const double* __restrict__ dx, const double* __restrict__ ds,
+                              int64_t n, double gamma, double* sc, double* bpart, unsigned* bcnt) {
+  const double xs = sc[SC_XS], B = sc[SC_B], C = sc[SC_C];
+  const double g1 = 1.0 - gamma;
+  const double nn = (double)n;
+  const double m0 = g1 * xs / nn, m1 = g1 * B / nn, m2 = g1 * C / nn;
+  double best = INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double xi = x[i], si = s[i], dxi = dx[i], dsi = ds[i];
+    const double r = first_crossing(xi * si - m0, xi * dsi + si * dxi - m1, dxi * dsi - m2);
+    best = fmin(best, r);
+  }
+  if (grid_min_last(best, bpart, bcnt) && threadIdx.x == 0) {
+    const double eta = sc[SC_ETA], mu0 = sc[SC_MU0];
+    double amax = fmin(1.0, best);
+    const double gr = first_crossing(xs / nn / mu0 - eta, B / nn / mu0 + eta, C / nn / mu0);
+    amax = fmin(amax, gr);
+    if (!(amax >= 0.0)) amax = 0.0;
+    // step (f): minimise f(a) = B a + C a^2 on [0, amax]
+    double alpha = amax;
+    double fbest = B * amax + C * amax * amax;
+    if (fbest > 0.0) {  // f(0) = 0 beats a positive endpoint; a tie keeps the larger a
+      alpha = 0.0;
+      fbest = 0.0;
+    }
+    if (C > 0.0) {
+      const double vtx = -B / (2.0 * C);
+      if (vtx > 0.0 && vtx < amax) {
+        const double fv = B * vtx + C * vtx * vtx;
+        if (fv < fbest) {
+          alpha = vtx;
+          fbest = fv;
+        }
+      }
+    }
+    sc[SC_AMAX] = amax;
+    sc[SC_STEP] = alpha;
+  }
+}
+
+cudaError_t launch_step_length(const double* x, const double* s, const double* dx,
+                               const double* ds, int64_t n, double gamma, double* sc,
+                               double* bpart, unsigned* bcnt, cudaStream_t st) {
+  k_step_length<<<vec_grid(n), 256, 0, st>>>(x, s, dx, ds, n, gamma, sc, bpart, bcnt);
+  return cudaGetLastError();
+}
+
+// Alg. 2 step (g).
+__global__ void k_apply_step(double* x, double* s, double* y, const double* dx, const double* ds,
+                             const double* dy, int64_t n, int m, const double* sc) {
+  const double al = sc[SC_STEP];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(al, dx[i], x[i]);
+    s[i] = fma(al, ds[i], s[i]);
+    if (i < m) y[i] = fma(al, dy[i], y[i]);
+  }
+}
+
+cudaError_t launch_apply_step(double* x, double* s, double* y, const double* dx, const double* ds,
+                              const double* dy, int64_t n, int m, const double* sc,
+                              cudaStream_t st) {
+  k_apply_step<<<vec_grid(n), 256, 0, st>>>(x, s, y, dx, ds, dy, n, m, sc);
+  return cudaGetLastError();
+}
+
+}  // namespace lpk

@@ -1,0 +1,840 @@
+// C ABI of the sketch-preconditioned infeasible IPM (include/lp.h): context management and
+// the host-side sequencing of the kernels for Algorithms 1 and 2.
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+using namespace lpk;
+
+static thread_local std::string g_err;
+
+void lp_set_error(const std::string& msg) { g_err = msg; }
+
+lp_status lp_cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return LP_ERR_CUDA;
+}
+
+static lp_status fail(lp_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define LP_TRY(expr)                    \
+  do {                                  \
+    lp_status s__ = (expr);             \
+    if (s__ != LP_OK) return s__;       \
+  } while (0)
+
+static size_t dtype_size(lp_dtype t) {
+  switch (t) {
+    case LP_F64: return 8;
+    case LP_F32: return 4;
+    case LP_BF16: return 2;
+    case LP_F16: return 2;
+  }
+  return 0;
+}
+
+static int round_up(int v, int q) { return (v + q - 1) / q * q; }
+
+extern "C" {
+
+const char* lp_last_error(void) { return g_err.c_str(); }
+
+const char* lp_status_str(lp_status st) {
+  switch (st) {
+    case LP_OK: return "LP_OK";
+    case LP_ERR_ARG: return "LP_ERR_ARG";
+    case LP_ERR_OOM: return "LP_ERR_OOM";
+    case LP_ERR_CUDA: return "LP_ERR_CUDA";
+    case LP_ERR_BREAKDOWN: return "LP_ERR_BREAKDOWN";
+    case LP_ERR_NOT_CONVERGED: return "LP_ERR_NOT_CONVERGED";
+    case LP_ERR_TIMEOUT: return "LP_ERR_TIMEOUT";
+    case LP_ERR_NUMERIC: return "LP_ERR_NUMERIC";
+  }
+  return "LP_ERR_UNKNOWN";
+}
+
+lp_status lp_params_default(lp_params* p) {
+  if (!p) return fail(LP_ERR_ARG, "lp_params_default: NULL");
+  p->tol = 1e-8;
+  p->cg_rel_tol = 1e-6;
+  p->sigma = 0.5;
+  p->gamma = 0.99;
+  p->cg_max_iter = 500;
+  p->ipm_max_iter = 200;
+  p->refine_max = 6;
+  p->sketch_s = 4;
+  p->sketch_w = 0;
+  p->cg_theory_rule = 1;
+  p->seed = 0;
+  p->stream_dtype = LP_F64;
+  p->cg_batch = 4;
+  return LP_OK;
+}
+
+}  // extern "C"
+
+static lp_status check_params(const lp_params& p, int m) {
+  if (!(p.tol > 0) || !(p.cg_rel_tol >= 0) || !(p.sigma > 0 && p.sigma < 0.8) ||
+      !(p.gamma > 0 && p.gamma < 1))
+    return fail(LP_ERR_ARG, "invalid tolerance, sigma (0, 4/5) or gamma (0, 1)");
+  if (p.cg_max_iter < 1 || p.ipm_max_iter < 0 || p.refine_max < 0 || p.cg_batch < 1)
+    return fail(LP_ERR_ARG, "invalid iteration caps");
+  if (p.sketch_s < 1 || p.sketch_w < 0) return fail(LP_ERR_ARG, "invalid sketch size");
+  const int w = p.sketch_w ? p.sketch_w : 4 * m;
+  if (w % p.sketch_s != 0) return fail(LP_ERR_ARG, "sketch_w must be a multiple of sketch_s");
+  if (w < m) return fail(LP_ERR_ARG, "sketch_w must be >= m");
+  if (w > (1 << 20)) return fail(LP_ERR_ARG, "sketch_w too large");
+  return LP_OK;
+}
+
+template <typename T>
+static lp_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return LP_OK;
+}
+
+static void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+extern "C" void lp_destroy(lp_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  if (c->own_As) dfree(c->As);
+  dfree(c->A);
+  if (c->own_svals) dfree(c->svals);
+  dfree(c->colptr);
+  dfree(c->rowidx);
+  dfree(c->vals);
+  void* bufs[] = {c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
+                  c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
+                  c->dyacc, c->rhs, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->G,
+                  c->u, c->Q, c->M, c->Pinv, c->T, c->C, c->Qsplit, c->sc, c->fl, c->bpart,
+                  c->bcnt};
+  for (void* p : bufs) dfree(p);
+  if (c->sc_h) cudaFreeHost(c->sc_h);
+  if (c->fl_h) cudaFreeHost(c->fl_h);
+  delete c;
+}
+
+static lp_status alloc_workspace(lp_ctx* c) {
+  const int m = c->m;
+  const int64_t n = c->n;
+  double** nvec[] = {&c->x, &c->s, &c->d2, &c->d, &c->rd, &c->t, &c->wu, &c->dx, &c->ds};
+  for (double** p : nvec) LP_TRY(dalloc(p, (size_t)n));
+  double** mvec[] = {&c->y, &c->rp, &c->p, &c->dy, &c->r, &c->z, &c->dd, &c->q, &c->rtil,
+                     &c->qhat, &c->res, &c->tm, &c->dyacc, &c->rhs};
+  for (double** p : mvec) LP_TRY(dalloc(p, (size_t)m));
+  const int maxgrid = std::max(coltile_max_grid(c->num_sms), csc_max_grid(c->num_sms));
+  c->part_bytes = (size_t)maxgrid * 2 * m * sizeof(double);
+  LP_TRY(dalloc((unsigned char**)&c->part, c->part_bytes));
+  // sketch
+  c->ss = c->prm.sketch_s;
+  c->w = c->prm.sketch_w ? c->prm.sketch_w : 4 * m;
+  LP_TRY(dalloc(&c->hb, (size_t)n * c->ss));
+  LP_TRY(dalloc(&c->list, (size_t)n * c->ss));
+  LP_TRY(dalloc(&c->cnt, (size_t)c->w + 1));
+  LP_TRY(dalloc(&c->start, (size_t)c->w + 1));
+  LP_TRY(dalloc(&c->cursor, (size_t)c->w + 1));
+  c->ldg = round_up(m, 2);
+  LP_TRY(dalloc(&c->G, (size_t)c->ldg * c->w));
+  LP_CU(cudaMemsetAsync(c->G, 0, (size_t)c->ldg * c->w * sizeof(double), c->st));
+  LP_TRY(dalloc(&c->u, (size_t)c->w));
+  // factor
+  c->mp = round_up(m, 64);
+  LP_TRY(dalloc(&c->Q, (size_t)c->mp * c->mp));
+  LP_TRY(dalloc(&c->M, (size_t)c->mp * c->mp));
+  LP_TRY(dalloc(&c->Pinv, (size_t)kNB * kNB));
+  LP_TRY(dalloc(&c->T, (size_t)kNB * c->mp));
+  LP_TRY(dalloc(&c->C, (size_t)c->mp * kNB));
+  c->qsplit = gram_split(m, c->w, c->num_sms);
+  const int nt = c->mp / 64;
+  LP_TRY(dalloc(&c->Qsplit, (size_t)c->qsplit * (nt * (nt + 1) / 2) * 64 * 64));
+  // scalars
+  LP_TRY(dalloc(&c->sc, SC_COUNT));
+  LP_TRY(dalloc(&c->fl, FL_COUNT));
+  LP_TRY(dalloc(&c->bpart, (size_t)kMaxRedBlocks * 8));
+  LP_TRY(dalloc(&c->bcnt, 16));
+  LP_CU(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), c->st));
+  LP_CU(cudaMemsetAsync(c->fl, 0, FL_COUNT * sizeof(int), c->st));
+  LP_CU(cudaMemsetAsync(c->bcnt, 0, 16 * sizeof(unsigned), c->st));
+  LP_CU(cudaMallocHost((void**)&c->sc_h, SC_COUNT * sizeof(double)));
+  LP_CU(cudaMallocHost((void**)&c->fl_h, FL_COUNT * sizeof(int)));
+  LP_CU(symv_set_smem(m));
+  return LP_OK;
+}
+
+static lp_status sync_scalars(lp_ctx* c) {
+  LP_CU(cudaMemcpyAsync(c->sc_h, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  LP_CU(cudaMemcpyAsync(c->fl_h, c->fl, FL_COUNT * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  LP_CU(cudaStreamSynchronize(c->st));
+  return LP_OK;
+}
+
+static lp_status check_finite_dev(lp_ctx* c, const void* p, lp_dtype dt, int64_t count,
+                                  const char* what) {
+  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_NUMERIC, 0, c->st));
+  LP_CU(launch_check_finite(p, dt, count, c->fl + FL_NUMERIC, c->st));
+  LP_TRY(sync_scalars(c));
+  if (c->fl_h[FL_NUMERIC]) return fail(LP_ERR_ARG, std::string(what) + " has NaN or Inf entries");
+  return LP_OK;
+}
+
+extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout layout,
+                               lp_dtype a_dtype, const void* A_vals, const int64_t* indptr,
+                               const int32_t* indices, int64_t nnz, const double* b,
+                               const double* cvec, const lp_params* prm, void* stream) {
+  if (!out) return fail(LP_ERR_ARG, "lp_create: out is NULL");
+  *out = nullptr;
+  if (m < 1 || n < m || m > 8192) return fail(LP_ERR_ARG, "lp_create: need 1 <= m <= n, m <= 8192");
+  if (n > ((int64_t)1 << 31) - 2) return fail(LP_ERR_ARG, "lp_create: n too large");
+  if (!A_vals || !b || !cvec) return fail(LP_ERR_ARG, "lp_create: NULL A, b or c");
+  if (a_dtype != LP_F64 && a_dtype != LP_F32)
+    return fail(LP_ERR_ARG, "lp_create: A must be LP_F64 or LP_F32");
+  if (layout == LP_CSR && (!indptr || !indices || nnz < 0))
+    return fail(LP_ERR_ARG, "lp_create: CSR needs indptr, indices and nnz");
+  if (layout != LP_CSR && layout != LP_DENSE_COLMAJOR && layout != LP_DENSE_ROWMAJOR)
+    return fail(LP_ERR_ARG, "lp_create: unknown layout");
+  lp_params p;
+  if (prm) p = *prm; else lp_params_default(&p);
+  LP_TRY(check_params(p, m));
+
+  lp_ctx* c = new lp_ctx();
+  c->m = m;
+  c->n = n;
+  c->prm = p;
+  c->st = (cudaStream_t)stream;
+  c->sparse = (layout == LP_CSR);
+  c->a_dtype = a_dtype;
+  lp_status st = LP_OK;
+  auto bail = [&](lp_status s) {
+    lp_destroy(c);
+    return s;
+  };
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e != cudaSuccess) return bail(lp_cuda_fail(e, "cudaGetDevice"));
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
+  if (e != cudaSuccess) return bail(lp_cuda_fail(e, "cudaDeviceGetAttribute"));
+
+  if ((st = alloc_workspace(c)) != LP_OK) return bail(st);
+  if ((st = dalloc(&c->b, m)) != LP_OK || (st = dalloc(&c->c, n)) != LP_OK) return bail(st);
+  e = cudaMemcpyAsync(c->b, b, m * sizeof(double), cudaMemcpyDefault, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->c, cvec, n * sizeof(double), cudaMemcpyDefault, c->st);
+  if (e != cudaSuccess) return bail(lp_cuda_fail(e, "copy b, c"));
+  if ((st = check_finite_dev(c, c->b, LP_F64, m, "b")) != LP_OK) return bail(st);
+  if ((st = check_finite_dev(c, c->c, LP_F64, n, "c")) != LP_OK) return bail(st);
+
+  const size_t es = dtype_size(a_dtype);
+  if (!c->sparse) {
+    // master copy: column-major, columns 16-byte aligned
+    c->lda = round_up(m, (int)(16 / es));
+    if ((st = dalloc((unsigned char**)&c->A, (size_t)c->lda * n * es)) != LP_OK) return bail(st);
+    if (layout == LP_DENSE_COLMAJOR) {
+      if (c->lda != m) {
+        e = cudaMemsetAsync(c->A, 0, (size_t)c->lda * n * es, c->st);
+        if (e != cudaSuccess) return bail(lp_cuda_fail(e, "memset A"));
+      }
+      e = cudaMemcpy2DAsync(c->A, c->lda * es, A_vals, m * es, m * es, n, cudaMemcpyDefault, c->st);
+      if (e != cudaSuccess) return bail(lp_cuda_fail(e, "copy A"));
+    } else {
+      unsigned char* tmp = nullptr;
+      if ((st = dalloc(&tmp, (size_t)m * n * es)) != LP_OK) return bail(st);
+      e = cudaMemcpyAsync(tmp, A_vals, (size_t)m * n * es, cudaMemcpyDefault, c->st);
+      if (e == cudaSuccess)
+        e = launch_convert_dense(tmp, a_dtype, true, m, n, c->A, a_dtype, c->lda, c->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+      cudaFree(tmp);
+      if (e != cudaSuccess) return bail(lp_cuda_fail(e, "row-major A"));
+    }
+    if ((st = check_finite_dev(c, c->A, a_dtype, (int64_t)c->lda * n, "A")) != LP_OK) return bail(st);
+    // streamed copy for the CG products
+    lp_dtype sd = p.stream_dtype == LP_F64 ? a_dtype : p.stream_dtype;
+    if (sd == LP_F64 && a_dtype == LP_F32) sd = LP_F32;
+    c->s_dtype = sd;
+    if (sd == a_dtype) {
+      c->As = c->A;
+      c->lda_s = c->lda;
+    } else {
+      c->lda_s = round_up(m, (int)(16 / dtype_size(sd)));
+      if ((st = dalloc((unsigned char**)&c->As, (size_t)c->lda_s * n * dtype_size(sd))) != LP_OK)
+        return bail(st);
+      c->own_As = true;
+      // convert from the master copy (column-major with leading dim lda): walk as an
+      // lda x n matrix, padding rows are zero already.
+      e = launch_convert_dense(c->A, a_dtype, false, c->lda, n, c->As, sd, c->lda_s, c->st);
+      if (e != cudaSuccess) return bail(lp_cuda_fail(e, "stream copy"));
+    }
+  } else {
+    c->nnz = nnz;
+    int64_t* ip = nullptr;
+    int32_t* ix = nullptr;
+    unsigned char* vv = nullptr;
+    int64_t* cur = nullptr;
+    if ((st = dalloc(&ip, (size_t)m + 1)) != LP_OK || (st = dalloc(&ix, (size_t)nnz)) != LP_OK ||
+        (st = dalloc(&vv, (size_t)nnz * es)) != LP_OK || (st = dalloc(&cur, (size_t)n)) != LP_OK ||
+        (st = dalloc(&c->colptr, (size_t)n + 1)) != LP_OK ||
+        (st = dalloc(&c->rowidx, (size_t)nnz)) != LP_OK ||
+        (st = dalloc((unsigned char**)&c->vals, (size_t)nnz * es)) != LP_OK) {
+      dfree(ip); dfree(ix); dfree(vv); dfree(cur);
+      return bail(st);
+    }
+    e = cudaMemcpyAsync(ip, indptr, (m + 1) * sizeof(int64_t), cudaMemcpyDefault, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ix, indices, nnz * sizeof(int32_t), cudaMemcpyDefault, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vv, A_vals, nnz * es, cudaMemcpyDefault, c->st);
+    // validate the structure on the host copy of indptr (small) and the indices on device
+    std::vector<int64_t> hip(m + 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hip.data(), ip, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    bool ok = (e == cudaSuccess) && hip[0] == 0 && hip[m] == nnz;
+    for (int i = 0; ok && i < m; ++i) ok = hip[i] <= hip[i + 1];
+    if (ok) {
+      // column ids in range: reuse the finiteness flag through a tiny check on host copy
+      std::vector<int32_t> hix(nnz);
+      if (cudaMemcpy(hix.data(), ix, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+      for (int64_t k = 0; ok && k < nnz; ++k) ok = hix[k] >= 0 && hix[k] < n;
+    }
+    if (ok) e = csr_to_csc(ip, ix, vv, a_dtype, m, n, nnz, c->colptr, cur, c->rowidx, c->vals, c->st);
+    if (ok && e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    dfree(ip); dfree(ix); dfree(vv); dfree(cur);
+    if (e != cudaSuccess) return bail(lp_cuda_fail(e, "CSR to CSC"));
+    if (!ok) return bail(fail(LP_ERR_ARG, "lp_create: malformed CSR (indptr or column ids)"));
+    if ((st = check_finite_dev(c, c->vals, a_dtype, nnz, "A")) != LP_OK) return bail(st);
+    c->svals = c->vals;
+    c->s_dtype = a_dtype;
+    if (p.stream_dtype == LP_F32 && a_dtype == LP_F64) {
+      // an FP32 copy of the values for the CG products
+      if ((st = dalloc((unsigned char**)&c->svals, (size_t)nnz * 4)) != LP_OK) return bail(st);
+      c->own_svals = true;
+      e = launch_convert_dense(c->vals, LP_F64, false, 1, nnz, c->svals, LP_F32, 1, c->st);
+      if (e != cudaSuccess) return bail(lp_cuda_fail(e, "stream values"));
+      c->s_dtype = LP_F32;
+    }
+  }
+  // norms of b and c for the stopping rule
+  LP_CU(launch_norm2(c->b, m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
+  if ((st = sync_scalars(c)) != LP_OK) return bail(st);
+  c->bnorm = sqrt(c->sc_h[SC_RES2]);
+  LP_CU(launch_norm2(c->c, n, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
+  if ((st = sync_scalars(c)) != LP_OK) return bail(st);
+  c->cnorm = sqrt(c->sc_h[SC_RES2]);
+  *out = c;
+  return LP_OK;
+}
+
+extern "C" lp_status lp_set_params(lp_ctx* c, const lp_params* prm) {
+  if (!c || !prm) return fail(LP_ERR_ARG, "lp_set_params: NULL");
+  LP_TRY(check_params(*prm, c->m));
+  const int w = prm->sketch_w ? prm->sketch_w : 4 * c->m;
+  if (w != c->w || prm->sketch_s != c->ss)
+    return fail(LP_ERR_ARG, "lp_set_params: sketch size is fixed at lp_create");
+  lp_dtype sd = prm->stream_dtype == LP_F64 ? c->a_dtype : prm->stream_dtype;
+  if (!c->sparse && sd != c->s_dtype && !(sd == LP_F64 && c->a_dtype == LP_F32))
+    return fail(LP_ERR_ARG, "lp_set_params: stream dtype is fixed at lp_create");
+  c->prm = *prm;
+  return LP_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Building blocks
+// ------------------------------------------------------------------------------------------
+
+// One pass y = A diag(w) A^T v (w == NULL: identity) with t = A^T v (optional).
+// precise: master copy with FP64 accumulation; else the streamed copy.
+static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const double* w, double* t,
+                             int red_mode, double* out, const double* p0, int skip_if_done,
+                             int* nblk_out = nullptr) {
+  int nblk;
+  bool acc64;
+  if (!c->sparse) {
+    ColArgs a{};
+    const lp_dtype ta = precise ? c->a_dtype : c->s_dtype;
+    a.A = precise ? c->A : c->As;
+    a.lda = precise ? c->lda : c->lda_s;
+    a.m = c->m;
+    a.n = c->n;
+    a.v = v;
+    a.d2 = w;
+    a.colout = t;
+    a.part = c->part;
+    a.fl = c->fl;
+    a.skip_if_done = skip_if_done;
+    acc64 = precise || ta == LP_F64;
+    nblk = launch_coltile(ta, acc64, MODE_NORMAL, a, c->num_sms, c->st);
+  } else {
+    CscArgs a{};
+    const lp_dtype tv = precise ? c->a_dtype : c->s_dtype;
+    a.colptr = c->colptr;
+    a.rowidx = c->rowidx;
+    a.vals = precise ? c->vals : c->svals;
+    a.m = c->m;
+    a.n = c->n;
+    a.v = v;
+    a.d2 = w;
+    a.colout = t;
+    a.part = c->part;
+    a.fl = c->fl;
+    a.skip_if_done = skip_if_done;
+    acc64 = precise || tv == LP_F64;
+    nblk = launch_csc(tv, acc64, MODE_NORMAL, a, c->num_sms, c->st);
+  }
+  if (nblk < 0) return fail(LP_ERR_ARG, "unsupported shape for the matrix pass");
+  LP_CU(cudaGetLastError());
+  RedArgs r{};
+  r.mode = red_mode;
+  r.part = c->part;
+  r.nblk = nblk;
+  r.nout = 1;
+  r.m = c->m;
+  r.acc_f64 = acc64;
+  r.out0 = out;
+  r.p0 = p0;
+  r.dvec = v;
+  r.sc = c->sc;
+  r.fl = c->fl;
+  r.bpart = c->bpart;
+  r.bcnt = c->bcnt;
+  r.skip_if_done = skip_if_done;
+  LP_CU(launch_reduce(r, c->st));
+  if (nblk_out) *nblk_out = nblk;
+  return LP_OK;
+}
+
+// Product with the sketch: out = G G^T v - p0 (red_mode MINUS_P) and u = G^T v.
+static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* u, double* out,
+                           const double* p0) {
+  ColArgs a{};
+  a.A = G;
+  a.lda = c->ldg;
+  a.m = c->m;
+  a.n = c->w;
+  a.v = v;
+  a.d2 = nullptr;
+  a.colout = u;
+  a.part = c->part;
+  a.fl = c->fl;
+  a.skip_if_done = 0;
+  const int nblk = launch_coltile(LP_F64, true, MODE_NORMAL, a, c->num_sms, c->st);
+  if (nblk < 0) return fail(LP_ERR_ARG, "unsupported shape for the sketch pass");
+  RedArgs r{};
+  r.mode = p0 ? RED_MINUS_P : RED_PLAIN;
+  r.part = c->part;
+  r.nblk = nblk;
+  r.nout = 1;
+  r.m = c->m;
+  r.acc_f64 = true;
+  r.out0 = out;
+  r.p0 = p0;
+  r.sc = c->sc;
+  r.fl = c->fl;
+  r.bpart = c->bpart;
+  r.bcnt = c->bcnt;
+  LP_CU(launch_reduce(r, c->st));
+  return LP_OK;
+}
+
+// Alg. 2 step (b): d2, d, mu from (x, s); r_p, r_d, p in one pass; ||r_p||^2, ||r_d||^2.
+static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, const double* s,
+                               double sigma, double* rp, double* rd, double* p) {
+  LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, sigma, c->c, c->st));
+  int nblk;
+  if (!c->sparse) {
+    ColArgs a{};
+    a.A = c->A;
+    a.lda = c->lda;
+    a.m = c->m;
+    a.n = c->n;
+    a.v = y;
+    a.x = x;
+    a.s = s;
+    a.c = c->c;
+    a.sc = c->sc;
+    a.colout = rd;
+    a.part = c->part;
+    a.fl = c->fl;
+    nblk = launch_coltile(c->a_dtype, true, MODE_RESID, a, c->num_sms, c->st);
+  } else {
+    CscArgs a{};
+    a.colptr = c->colptr;
+    a.rowidx = c->rowidx;
+    a.vals = c->vals;
+    a.m = c->m;
+    a.n = c->n;
+    a.v = y;
+    a.x = x;
+    a.s = s;
+    a.c = c->c;
+    a.sc = c->sc;
+    a.colout = rd;
+    a.part = c->part;
+    a.fl = c->fl;
+    nblk = launch_csc(c->a_dtype, true, MODE_RESID, a, c->num_sms, c->st);
+  }
+  if (nblk < 0) return fail(LP_ERR_ARG, "unsupported shape for the residual pass");
+  LP_CU(cudaGetLastError());
+  RedArgs r{};
+  r.mode = RED_RESID;
+  r.part = c->part;
+  r.nblk = nblk;
+  r.nout = 2;
+  r.m = c->m;
+  r.acc_f64 = true;
+  r.out0 = rp;
+  r.out1 = p;
+  r.p0 = c->b;
+  r.sc = c->sc;
+  r.fl = c->fl;
+  r.bpart = c->bpart;
+  r.bcnt = c->bcnt;
+  LP_CU(launch_reduce(r, c->st));
+  LP_CU(launch_norm2(rd, c->n, c->sc, SC_RD2, c->bpart, c->bcnt, c->st));
+  return LP_OK;
+}
+
+// Alg. 1 step 1 / Alg. 2 step (a): G = A D W(seed, k).
+static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
+  LP_CU(cudaMemsetAsync(c->cnt, 0, (c->w + 1) * sizeof(int32_t), c->st));
+  LP_CU(launch_sketch_hash(c->prm.seed, k, c->n, c->ss, c->w, c->hb, c->cnt, nullptr, nullptr, c->st));
+  LP_CU(launch_sketch_scan(c->cnt, c->w, c->start, c->cursor, c->st));
+  LP_CU(launch_sketch_scatter(c->hb, c->n, c->ss, c->start, c->cursor, c->list, c->st));
+  if (!c->sparse) {
+    LP_CU(launch_sketch_gather_dense(c->a_dtype, c->A, c->lda, c->m, c->ss, c->w, c->start,
+                                     c->list, d, G, c->ldg, c->st));
+  } else {
+    LP_CU(launch_sketch_gather_csc(c->a_dtype, c->colptr, c->rowidx, c->vals, c->m, c->ss, c->w,
+                                   c->start, c->list, d, G, c->ldg, c->st));
+  }
+  return LP_OK;
+}
+
+// Alg. 1 step 2: Q = G G^T, M = Q^{-1}.
+static lp_status run_factor(lp_ctx* c, const double* G) {
+  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
+  LP_CU(launch_gram(G, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
+  LP_CU(cudaMemcpyAsync(c->M, c->Q, (size_t)c->mp * c->mp * sizeof(double),
+                        cudaMemcpyDeviceToDevice, c->st));
+  LP_CU(launch_gj_inverse(c->M, c->Q, c->mp, c->Pinv, c->T, c->C, c->fl, c->st));
+  LP_TRY(sync_scalars(c));
+  if (c->fl_h[FL_BREAK])
+    return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (non-positive pivot)");
+  return LP_OK;
+}
+
+// PCG (Alg. 1 step 3) on (A D^2 A^T) delta = rhs with preconditioner Q, from delta = 0.
+// Stops when rho_j <= min(rel^2 rho_0, abs_thr^2) or after cg_max_iter products.
+static lp_status run_pcg(lp_ctx* c, const double* rhs, double* delta, double abs_thr,
+                         int* iters, double* rho0_out, double* rho_out) {
+  const int m = c->m;
+  LP_CU(launch_vec_ops(VOP_ZERO, delta, nullptr, nullptr, m, nullptr, c->st));
+  LP_CU(launch_vec_ops(VOP_COPY, c->r, rhs, nullptr, m, nullptr, c->st));
+  const double thr2 = isfinite(abs_thr) ? abs_thr * abs_thr : INFINITY;
+  LP_CU(launch_set(c->sc, SC_THR2, thr2, c->fl, FL_MAXIT, c->prm.cg_max_iter, c->st));
+  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_NUMERIC, 0, c->st));
+  LP_CU(launch_symv_init(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt,
+                         c->prm.cg_rel_tol, c->st));
+  LP_CU(launch_vec_ops(VOP_COPY, c->dd, c->z, nullptr, m, nullptr, c->st));
+  for (;;) {
+    for (int b = 0; b < c->prm.cg_batch; ++b) {
+      LP_TRY(pass_normal(c, false, c->dd, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1));
+      LP_CU(launch_cg_axpy(delta, c->r, c->dd, c->q, m, c->sc, c->fl, c->st));
+      LP_CU(launch_symv_dot(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt,
+                            SYMV_CG_STEP, c->st));
+      LP_CU(launch_cg_dir(c->dd, c->z, m, c->sc, c->fl, c->st));
+    }
+    LP_TRY(sync_scalars(c));
+    if (c->fl_h[FL_DONE]) break;
+  }
+  *iters = c->fl_h[FL_ITERS];
+  if (rho0_out) *rho0_out = c->sc_h[SC_RHO0];
+  if (rho_out) *rho_out = c->sc_h[SC_RHO];
+  if (c->fl_h[FL_NUMERIC]) return fail(LP_ERR_NUMERIC, "CG met non-positive curvature or NaN");
+  return LP_OK;
+}
+
+struct SolveOut {
+  int cg_iters = 0;
+  int refine = 0;
+  double f_norm = 0.0;
+};
+
+// Alg. 1 (sketch, factor, PCG with FP64 residual refinement) and the FP64 correction data of
+// Eq. compv for the current d2 / d (prepared by launch_prep_iterate).  Results:
+//   c->dyacc = dy,  c->rtil = A D^2 A^T dy - p,  c->t = A^T dy,  c->u = (A D W)^dagger r~.
+static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, SolveOut* so) {
+  const int m = c->m;
+  LP_TRY(run_sketch(c, c->d, k, c->G));
+  LP_TRY(run_factor(c, c->G));
+  double abs_thr = INFINITY;
+  if (c->prm.cg_theory_rule)
+    abs_thr = c->prm.gamma * c->prm.sigma * sqrt(mu) / (4.0 * sqrt((double)c->n));
+  const bool lowprec = c->s_dtype != c->a_dtype;
+  double rho0 = 0.0, target2 = 0.0;
+  int total_it = 0, outer = 0;
+  for (;;) {
+    int it = 0;
+    double r0 = 0.0, rl = 0.0;
+    if (outer == 0) {
+      LP_TRY(run_pcg(c, p, c->dyacc, abs_thr, &it, &r0, &rl));
+      rho0 = r0;
+      target2 = std::min(c->prm.cg_rel_tol * c->prm.cg_rel_tol * rho0,
+                         isfinite(abs_thr) ? abs_thr * abs_thr : INFINITY);
+    } else {
+      // refinement: solve (A D^2 A^T) delta = -r~ and add it to dy
+      LP_CU(launch_vec_ops(VOP_NEG, c->rhs, c->rtil, nullptr, m, nullptr, c->st));
+      LP_TRY(run_pcg(c, c->rhs, c->dy, abs_thr, &it, &r0, &rl));
+      LP_CU(launch_vec_ops(VOP_ADD, c->dyacc, c->dyacc, c->dy, m, nullptr, c->st));
+    }
+    total_it += it;
+    // r~ = A D^2 A^T dy - p in FP64 from the input-precision A, with t = A^T dy
+    LP_TRY(pass_normal(c, true, c->dyacc, c->d2, c->t, RED_MINUS_P, c->rtil, p, 0));
+    // ||f||^2 = r~^T Q^{-1} r~; qhat = Q^{-1} r~ starts the correction
+    LP_CU(launch_symv_dot(c->M, c->mp, m, c->rtil, c->qhat, c->sc, c->fl, c->bpart, c->bcnt,
+                          SYMV_F2, c->st));
+    LP_TRY(sync_scalars(c));
+    const double f2 = c->sc_h[SC_F2];
+    if (!isfinite(f2)) return fail(LP_ERR_NUMERIC, "non-finite residual in the normal solve");
+    so->f_norm = sqrt(std::max(f2, 0.0));
+    if (!lowprec || f2 <= 4.0 * target2 || outer >= c->prm.refine_max) break;
+    ++outer;
+  }
+  so->cg_iters = total_it;
+  // u = (A D W)^T Q^{-1} r~, refining Q^{-1} r~ against Q = G G^T in FP64
+  double prev = INFINITY;
+  int steps = 0;
+  for (;;) {
+    LP_TRY(pass_gram(c, c->G, c->qhat, c->u, c->res, c->rtil));   // res = G G^T qhat - r~
+    LP_CU(launch_norm2(c->res, m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
+    LP_TRY(sync_scalars(c));
+    const double nr = sqrt(c->sc_h[SC_RES2]);
+    if (!isfinite(nr)) return fail(LP_ERR_NUMERIC, "non-finite correction residual");
+    if (nr == 0.0 || nr >= 0.5 * prev || steps >= c->prm.refine_max) break;
+    LP_CU(launch_symv_dot(c->M, c->mp, m, c->res, c->tm, c->sc, c->fl, c->bpart, c->bcnt,
+                          SYMV_PLAIN, c->st));
+    LP_CU(launch_vec_ops(VOP_SUB, c->qhat, c->qhat, c->tm, m, nullptr, c->st));
+    prev = nr;
+    ++steps;
+  }
+  so->refine = steps + outer;
+  return LP_OK;
+}
+
+// Alg. 2 steps (d)-(g) with W u gathered from the hashed W (or given).
+static lp_status run_step(lp_ctx* c, double* x, double* y, double* s, const double* rd,
+                          const double* dy, const double* t, const double* wu_given, double eta,
+                          double mu0, double* dx, double* ds) {
+  LP_CU(launch_set(c->sc, SC_ETA, eta, nullptr, 0, 0, c->st));
+  LP_CU(launch_set(c->sc, SC_MU0, mu0, nullptr, 0, 0, c->st));
+  double* wu = wu_given ? const_cast<double*>(wu_given) : c->wu;
+  LP_CU(launch_update_dirs(x, s, c->d2, c->d, rd, t, c->hb, c->ss, c->u, c->n, wu, dx, ds,
+                           wu_given ? 1 : 0, c->sc, c->bpart, c->bcnt, c->st));
+  LP_CU(launch_step_length(x, s, dx, ds, c->n, c->prm.gamma, c->sc, c->bpart, c->bcnt, c->st));
+  LP_CU(launch_apply_step(x, s, y, dx, ds, dy, c->n, c->m, c->sc, c->st));
+  return LP_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Entry points
+// ------------------------------------------------------------------------------------------
+
+extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, int32_t start_given,
+                                  lp_info* info) {
+  if (!c || !x || !y || !s) return fail(LP_ERR_ARG, "lp_ipm_solve: NULL argument");
+  const int m = c->m;
+  const int64_t n = c->n;
+  lp_info inf{};
+  if (start_given) {
+    LP_CU(cudaMemcpyAsync(c->x, x, n * sizeof(double), cudaMemcpyDefault, c->st));
+    LP_CU(cudaMemcpyAsync(c->y, y, m * sizeof(double), cudaMemcpyDefault, c->st));
+    LP_CU(cudaMemcpyAsync(c->s, s, n * sizeof(double), cudaMemcpyDefault, c->st));
+  } else {
+    std::vector<double> ones(std::max<int64_t>(n, 1), 1.0);
+    LP_CU(cudaMemcpyAsync(c->x, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    LP_CU(cudaMemcpyAsync(c->s, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    LP_CU(cudaMemsetAsync(c->y, 0, m * sizeof(double), c->st));
+    LP_CU(cudaStreamSynchronize(c->st));
+  }
+  const double sigma = c->prm.sigma;
+  LP_TRY(run_residuals(c, c->x, c->y, c->s, sigma, c->rp, c->rd, c->p));
+  LP_TRY(sync_scalars(c));
+  const double mu0 = c->sc_h[SC_MU];
+  const double r0 = sqrt(c->sc_h[SC_RP2] + c->sc_h[SC_RD2]);
+  lp_status result = LP_ERR_NOT_CONVERGED;
+  int k = 0;
+  for (;;) {
+    const double mu = c->sc_h[SC_MU];
+    const double rpn = sqrt(c->sc_h[SC_RP2]), rdn = sqrt(c->sc_h[SC_RD2]);
+    const double cx = c->sc_h[SC_CX];
+    inf.rp_rel = rpn / (1.0 + c->bnorm);
+    inf.rd_rel = rdn / (1.0 + c->cnorm);
+    inf.gap_rel = (double)n * mu / (1.0 + fabs(cx));
+    inf.mu = mu;
+    inf.obj = cx;
+    if (!isfinite(mu) || !isfinite(rpn) || !isfinite(rdn)) {
+      result = fail(LP_ERR_NUMERIC, "non-finite iterate");
+      break;
+    }
+    if (std::max(inf.rp_rel, std::max(inf.rd_rel, inf.gap_rel)) <= c->prm.tol) {
+      result = LP_OK;
+      break;
+    }
+    if (k >= c->prm.ipm_max_iter) {
+      result = fail(LP_ERR_NOT_CONVERGED, "IPM iteration cap reached");
+      break;
+    }
+    const double eta = r0 > 0 ? sqrt(rpn * rpn + rdn * rdn) / r0 : 0.0;
+    SolveOut so;
+    lp_status st = run_normal_solve(c, c->p, k, mu, &so);
+    if (st != LP_OK) {
+      result = st;
+      break;
+    }
+    inf.cg_iters_total += so.cg_iters;
+    inf.cg_iters_last = so.cg_iters;
+    inf.refine_steps = so.refine;
+    inf.f_norm = so.f_norm;
+    st = run_step(c, c->x, c->y, c->s, c->rd, c->dyacc, c->t, nullptr, eta, mu0, c->dx, c->ds);
+    if (st != LP_OK) {
+      result = st;
+      break;
+    }
+    ++k;
+    st = run_residuals(c, c->x, c->y, c->s, sigma, c->rp, c->rd, c->p);
+    if (st == LP_OK) st = sync_scalars(c);
+    if (st != LP_OK) {
+      result = st;
+      break;
+    }
+    inf.alpha_max = c->sc_h[SC_AMAX];
+    inf.alpha = c->sc_h[SC_STEP];
+    inf.v_norm = sqrt(c->sc_h[SC_V2]);
+  }
+  inf.ipm_iters = k;
+  inf.status = result;
+  LP_CU(cudaMemcpyAsync(x, c->x, n * sizeof(double), cudaMemcpyDefault, c->st));
+  LP_CU(cudaMemcpyAsync(y, c->y, m * sizeof(double), cudaMemcpyDefault, c->st));
+  LP_CU(cudaMemcpyAsync(s, c->s, n * sizeof(double), cudaMemcpyDefault, c->st));
+  LP_CU(cudaStreamSynchronize(c->st));
+  if (info) *info = inf;
+  return result;
+}
+
+extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s, const double* p,
+                                     int32_t k, double* dy, double* rtil, double* u, double* Wu,
+                                     double* Atdy, lp_info* info) {
+  if (!c || !x || !s || !p || !dy) return fail(LP_ERR_ARG, "lp_normal_solve: NULL argument");
+  if (k < 0) return fail(LP_ERR_ARG, "lp_normal_solve: k < 0");
+  LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
+                            c->c, c->st));
+  LP_TRY(sync_scalars(c));
+  const double mu = c->sc_h[SC_MU];
+  if (!(mu > 0) || !isfinite(mu)) return fail(LP_ERR_ARG, "lp_normal_solve: x, s must be positive");
+  LP_CU(cudaMemcpyAsync(c->rhs, p, c->m * sizeof(double), cudaMemcpyDefault, c->st));
+  // run_normal_solve uses c->rhs as scratch in refinement: keep p in rp
+  LP_CU(cudaMemcpyAsync(c->rp, p, c->m * sizeof(double), cudaMemcpyDefault, c->st));
+  SolveOut so;
+  LP_TRY(run_normal_solve(c, c->rp, k, mu, &so));
+  LP_CU(cudaMemcpyAsync(dy, c->dyacc, c->m * sizeof(double), cudaMemcpyDefault, c->st));
+  if (rtil) LP_CU(cudaMemcpyAsync(rtil, c->rtil, c->m * sizeof(double), cudaMemcpyDefault, c->st));
+  if (u) LP_CU(cudaMemcpyAsync(u, c->u, c->w * sizeof(double), cudaMemcpyDefault, c->st));
+  if (Atdy) LP_CU(cudaMemcpyAsync(Atdy, c->t, c->n * sizeof(double), cudaMemcpyDefault, c->st));
+  if (Wu) LP_CU(launch_apply_W(c->hb, c->ss, c->u, c->n, Wu, c->st));
+  LP_CU(cudaStreamSynchronize(c->st));
+  if (info) {
+    lp_info inf{};
+    inf.cg_iters_last = so.cg_iters;
+    inf.cg_iters_total = so.cg_iters;
+    inf.refine_steps = so.refine;
+    inf.f_norm = so.f_norm;
+    inf.mu = mu;
+    *info = inf;
+  }
+  return LP_OK;
+}
+
+extern "C" lp_status lp_residuals(lp_ctx* c, const double* x, const double* y, const double* s,
+                                  double sigma, double* rp, double* rd, double* p, double* mu_out) {
+  if (!c || !x || !y || !s || !rp || !rd || !p) return fail(LP_ERR_ARG, "lp_residuals: NULL argument");
+  LP_TRY(run_residuals(c, x, y, s, sigma, rp, rd, p));
+  LP_TRY(sync_scalars(c));
+  if (mu_out) *mu_out = c->sc_h[SC_MU];
+  return LP_OK;
+}
+
+extern "C" lp_status lp_sketch_indices(uint64_t seed, int32_t k, int64_t n, int32_t s, int32_t w,
+                                       int32_t* bucket, int8_t* sign, void* stream) {
+  if (n < 0 || s < 1 || w < 1 || w % s != 0 || k < 0)
+    return fail(LP_ERR_ARG, "lp_sketch_indices: need n >= 0, s >= 1, w % s == 0, k >= 0");
+  if (n == 0) return LP_OK;
+  if (!bucket || !sign) return fail(LP_ERR_ARG, "lp_sketch_indices: NULL output");
+  LP_CU(launch_sketch_hash(seed, k, n, s, w, nullptr, nullptr, bucket, sign, (cudaStream_t)stream));
+  return LP_OK;
+}
+
+extern "C" lp_status lp_sketch(lp_ctx* c, const double* d, int32_t k, double* G) {
+  if (!c || !d || !G || k < 0) return fail(LP_ERR_ARG, "lp_sketch: bad argument");
+  LP_TRY(run_sketch(c, d, k, c->G));
+  LP_CU(cudaMemcpy2DAsync(G, c->m * sizeof(double), c->G, c->ldg * sizeof(double),
+                          c->m * sizeof(double), c->w, cudaMemcpyDefault, c->st));
+  LP_CU(cudaStreamSynchronize(c->st));
+  return LP_OK;
+}
+
+extern "C" lp_status lp_factor(lp_ctx* c, const double* G, double* Q, double* Minv) {
+  if (!c || !G) return fail(LP_ERR_ARG, "lp_factor: NULL argument");
+  LP_CU(cudaMemcpy2DAsync(c->G, c->ldg * sizeof(double), G, c->m * sizeof(double),
+                          c->m * sizeof(double), c->w, cudaMemcpyDefault, c->st));
+  LP_TRY(run_factor(c, c->G));
+  const size_t row = c->m * sizeof(double), pitch = c->mp * sizeof(double);
+  if (Q) LP_CU(cudaMemcpy2DAsync(Q, row, c->Q, pitch, row, c->m, cudaMemcpyDefault, c->st));
+  if (Minv) LP_CU(cudaMemcpy2DAsync(Minv, row, c->M, pitch, row, c->m, cudaMemcpyDefault, c->st));
+  LP_CU(cudaStreamSynchronize(c->st));
+  return LP_OK;
+}
+
+extern "C" lp_status lp_normal_matvec(lp_ctx* c, const double* d2, const double* v, double* y,
+                                      double* t, lp_dtype stream_dtype) {
+  if (!c || !d2 || !v || !y) return fail(LP_ERR_ARG, "lp_normal_matvec: NULL argument");
+  bool precise;
+  if (stream_dtype == LP_F64) {
+    precise = true;
+  } else if (stream_dtype == c->s_dtype) {
+    precise = false;
+  } else {
+    return fail(LP_ERR_ARG, "lp_normal_matvec: stream dtype differs from the context's");
+  }
+  LP_TRY(pass_normal(c, precise, v, d2, t, RED_PLAIN, y, nullptr, 0));
+  LP_CU(cudaStreamSynchronize(c->st));
+  return LP_OK;
+}
+
+extern "C" lp_status lp_step(lp_ctx* c, double* x, double* y, double* s, const double* rd,
+                             const double* dy, const double* Atdy, const double* Wu, double mu,
+                             double eta, double mu0, double* dx, double* ds, double* out) {
+  if (!c || !x || !y || !s || !rd || !dy || !Atdy || !Wu) return fail(LP_ERR_ARG, "lp_step: NULL argument");
+  if (!(mu0 > 0)) return fail(LP_ERR_ARG, "lp_step: mu0 must be positive");
+  LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
+                            c->c, c->st));
+  (void)mu;  // mu is recomputed from x and s on the device
+  LP_TRY(run_step(c, x, y, s, rd, dy, Atdy, Wu, eta, mu0, dx ? dx : c->dx, ds ? ds : c->ds));
+  LP_TRY(sync_scalars(c));
+  if (out) {
+    out[0] = c->sc_h[SC_AMAX];
+    out[1] = c->sc_h[SC_STEP];
+    out[2] = c->sc_h[SC_B];
+    out[3] = c->sc_h[SC_C];
+  }
+  return LP_OK;
+}

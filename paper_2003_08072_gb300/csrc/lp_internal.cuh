@@ -1,0 +1,285 @@
+// Internal declarations of the sm_103a LP library: context, scalar slots, kernel launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lp.h"
+
+namespace lpk {
+
+// ---- device scalar slots (double sc[SC_COUNT]) ---------------------------------------
+enum Scalar {
+  SC_MU = 0,      // x^T s / n
+  SC_XS,          // x^T s
+  SC_SIGMU,       // sigma * mu
+  SC_RP2,         // ||r_p||^2
+  SC_RD2,         // ||r_d||^2
+  SC_CX,          // c^T x
+  SC_RHO,         // CG rho_j = r^T Q^{-1} r
+  SC_RHO0,        // rho_0 of the current CG solve
+  SC_THR2,        // squared CG stop threshold on rho
+  SC_ALPHA,       // CG alpha
+  SC_BETA,        // CG beta
+  SC_DQ,          // d^T q
+  SC_B,           // x^T ds + s^T dx
+  SC_C,           // dx^T ds
+  SC_AMAX,        // alpha_max
+  SC_STEP,        // alpha
+  SC_V2,          // ||v||^2
+  SC_V1,          // 1^T v
+  SC_RES2,        // squared norm of a refinement residual
+  SC_F2,          // r~^T Q^{-1} r~  (||f^(t)||^2)
+  SC_ETA,         // ||r|| / ||r^0||
+  SC_MU0,         // mu_0
+  SC_AMIN,        // per-element min crossing (internal)
+  SC_COUNT = 32
+};
+
+enum Flag {
+  FL_DONE = 0,   // CG finished (converged or capped)
+  FL_ITERS,      // CG iterations of the current solve
+  FL_NUMERIC,    // non-finite or non-positive curvature seen
+  FL_BREAK,      // non-positive pivot in the factorization
+  FL_MAXIT,      // CG iteration cap of the current solve
+  FL_COUNT = 8
+};
+
+constexpr int kNB = 32;          // block size of the Gauss-Jordan inverse
+constexpr int kMaxRedBlocks = 1024;
+
+}  // namespace lpk
+
+struct lp_ctx {
+  int m = 0;
+  int64_t n = 0;
+  bool sparse = false;
+  lp_params prm{};
+  cudaStream_t st = nullptr;
+  int dev = 0;
+  int num_sms = 0;
+
+  // dense matrix, column-major, 16-byte aligned columns (zero padded rows m..lda-1)
+  lp_dtype a_dtype = LP_F64;   // master copy dtype (F64 or F32)
+  void* A = nullptr;
+  int lda = 0;
+  lp_dtype s_dtype = LP_F64;   // streamed copy dtype used by the CG matvec
+  void* As = nullptr;          // == A when s_dtype == a_dtype
+  int lda_s = 0;
+  bool own_As = false;
+
+  // CSC (sparse) copy: column pointers, row ids, values
+  int64_t nnz = 0;
+  int64_t* colptr = nullptr;
+  int32_t* rowidx = nullptr;
+  void* vals = nullptr;        // a_dtype (F32 or F64)
+  void* svals = nullptr;       // stream dtype values (== vals or bf16/f16 copy)
+  bool own_svals = false;
+
+  double* b = nullptr;
+  double* c = nullptr;
+  double bnorm = 0, cnorm = 0;
+
+  // n-vectors
+  double *x = nullptr, *y = nullptr, *s = nullptr, *d2 = nullptr, *d = nullptr;
+  double *rd = nullptr, *t = nullptr, *wu = nullptr, *dx = nullptr, *ds = nullptr;
+  // m-vectors
+  double *rp = nullptr, *p = nullptr, *dy = nullptr, *r = nullptr, *z = nullptr, *dd = nullptr;
+  double *q = nullptr, *rtil = nullptr, *qhat = nullptr, *res = nullptr, *tm = nullptr;
+  double *dyacc = nullptr, *rhs = nullptr;
+
+  // per-CTA partials of the column-tile kernels
+  void* part = nullptr;
+  size_t part_bytes = 0;
+
+  // sketch
+  int w = 0, ss = 0;
+  int32_t* hb = nullptr;       // n*s packed (bucket | sign bit 31)
+  int32_t* cnt = nullptr;      // w + 1
+  int32_t* start = nullptr;    // w + 1
+  int32_t* cursor = nullptr;   // w
+  int32_t* list = nullptr;     // n*s entries: column | sign bit 31
+  double* G = nullptr;         // m x w column-major, leading dimension ldg (even)
+  int ldg = 0;
+  double* u = nullptr;         // w
+
+  // factor
+  int mp = 0;                  // m rounded up to kNB
+  double* Q = nullptr;         // mp x mp row-major (full symmetric)
+  double* M = nullptr;         // Q^{-1}, mp x mp row-major (full symmetric)
+  double* Pinv = nullptr;      // kNB x kNB
+  double* T = nullptr;         // kNB x mp
+  double* C = nullptr;         // mp x kNB
+  double* Qsplit = nullptr;    // split-k partials of the Gram product
+  int qsplit = 1;
+
+  // scalars
+  double* sc = nullptr;        // device SC_COUNT
+  int* fl = nullptr;           // device FL_COUNT
+  double* bpart = nullptr;     // last-block reduction partials (kMaxRedBlocks * 8)
+  unsigned* bcnt = nullptr;    // last-block counters (16)
+  double* sc_h = nullptr;      // pinned host mirror of sc
+  int* fl_h = nullptr;         // pinned host mirror of fl
+};
+
+// ---------------------------------------------------------------------------------------
+// error reporting (lp_api.cu)
+void lp_set_error(const std::string& msg);
+lp_status lp_cuda_fail(cudaError_t e, const char* what);
+
+#define LP_CU(call)                                   \
+  do {                                                \
+    cudaError_t e__ = (call);                         \
+    if (e__ != cudaSuccess) return lp_cuda_fail(e__, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// launchers (each enqueues on ctx->st and returns cudaGetLastError())
+namespace lpk {
+
+enum ColMode { MODE_NORMAL = 0, MODE_RESID = 1 };
+
+// y-partials of  sum_i a_i * coef_i  over column tiles of a dense column-major matrix.
+struct ColArgs {
+  const void* A;
+  int64_t lda;
+  int m;
+  int64_t n;
+  int64_t ntiles;
+  const double* v;     // m-vector for the column dots
+  const double* d2;    // NORMAL: per-column weight (NULL = 1)
+  const double* x;     // RESID
+  const double* s;     // RESID
+  const double* c;     // RESID
+  const double* sc;    // device scalars (RESID reads SC_SIGMU)
+  double* colout;      // NORMAL: t = A^T v (may be NULL); RESID: r_d
+  void* part;          // [grid][nout][m] partials (accumulator type)
+  const int* fl;       // skip everything when fl[FL_DONE] != 0 and skip_if_done
+  int skip_if_done;
+};
+
+// Dense column-tile pass.  acc_f64 selects FP64 accumulation (else FP32).
+// Returns the number of CTAs used (partials rows), or -1 on an unsupported shape.
+int launch_coltile(lp_dtype ta, bool acc_f64, int mode, ColArgs a, int num_sms, cudaStream_t st);
+
+// Sparse (CSC) passes
+struct CscArgs {
+  const int64_t* colptr;
+  const int32_t* rowidx;
+  const void* vals;
+  int m;
+  int64_t n;
+  const double* v;
+  const double* d2;
+  const double* x;
+  const double* s;
+  const double* c;
+  const double* sc;
+  double* colout;
+  void* part;          // [grid][nout][m]
+  const int* fl;
+  int skip_if_done;
+};
+int launch_csc(lp_dtype tv, bool acc_f64, int mode, CscArgs a, int num_sms, cudaStream_t st);
+
+// sum partials: out[o][i] = sum_b part[b][o][i]; modes below
+enum RedMode { RED_PLAIN = 0, RED_MINUS_P = 1, RED_RESID = 2, RED_CG_Q = 3 };
+struct RedArgs {
+  int mode;
+  const void* part;
+  int nblk;
+  int nout;
+  int m;
+  bool acc_f64;
+  double* out0;        // PLAIN: y; MINUS_P: y - p0; RESID: r_p = Ax - b; CG_Q: q
+  double* out1;        // RESID: p = b - A g
+  const double* p0;    // MINUS_P: subtrahend; RESID: b
+  const double* dvec;  // CG_Q: d (for d^T q)
+  double* sc;
+  int* fl;
+  double* bpart;
+  unsigned* bcnt;
+  int skip_if_done;
+};
+cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st);
+
+// n-vector kernels
+cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
+                                double* sc, double* bpart, unsigned* bcnt, double sigma,
+                                const double* c, cudaStream_t st);
+cudaError_t launch_norm2(const double* v, int64_t n, double* sc, int slot, double* bpart,
+                         unsigned* bcnt, cudaStream_t st);
+
+// sketch
+cudaError_t launch_sketch_hash(uint64_t seed, int k, int64_t n, int s, int w, int32_t* hb,
+                               int32_t* cnt, int32_t* bucket_out, int8_t* sign_out, cudaStream_t st);
+cudaError_t launch_sketch_scan(const int32_t* cnt, int w, int32_t* start, int32_t* cursor,
+                               cudaStream_t st);
+cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, const int32_t* start,
+                                  int32_t* cursor, int32_t* list, cudaStream_t st);
+cudaError_t launch_sketch_gather_dense(lp_dtype ta, const void* A, int64_t lda, int m, int s,
+                                       int w, const int32_t* start, const int32_t* list,
+                                       const double* d, double* G, int ldg, cudaStream_t st);
+cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const int32_t* rowidx,
+                                     const void* vals, int m, int s, int w, const int32_t* start,
+                                     const int32_t* list, const double* d, double* G, int ldg,
+                                     cudaStream_t st);
+
+// factor
+cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* Q, double* Qsplit,
+                        int split, cudaStream_t st);
+cudaError_t launch_gj_inverse(double* M, const double* Q0, int mp, double* Pinv, double* T,
+                              double* C, int* fl, cudaStream_t st);
+
+// CG / preconditioner
+cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, double* z,
+                            double* sc, int* fl, double* bpart, unsigned* bcnt, int mode,
+                            cudaStream_t st);
+enum SymvMode { SYMV_PLAIN = 0, SYMV_CG_INIT = 1, SYMV_CG_STEP = 2, SYMV_F2 = 3 };
+cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, double* z,
+                             double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
+                             cudaStream_t st);
+cudaError_t symv_set_smem(int m);
+int coltile_max_grid(int num_sms);
+int csc_max_grid(int num_sms);
+cudaError_t launch_cg_axpy(double* dy, double* r, const double* d, const double* q, int m,
+                           const double* sc, const int* fl, cudaStream_t st);
+cudaError_t launch_cg_dir(double* d, const double* z, int m, const double* sc, const int* fl,
+                          cudaStream_t st);
+cudaError_t launch_vec_ops(int op, double* a, const double* b, const double* c, int m,
+                           const double* sc, cudaStream_t st);
+enum VecOp { VOP_COPY = 0, VOP_ZERO = 1, VOP_ADD = 2, VOP_SUB = 3, VOP_NEG = 4 };
+
+// IPM update
+cudaError_t launch_update_dirs(const double* x, const double* s, const double* d2, const double* d,
+                               const double* rd, const double* t, const int32_t* hb, int ss,
+                               const double* u, int64_t n, double* wu, double* dx, double* ds,
+                               int wu_given, double* sc, double* bpart, unsigned* bcnt,
+                               cudaStream_t st);
+cudaError_t launch_step_length(const double* x, const double* s, const double* dx,
+                               const double* ds, int64_t n, double gamma, double* sc,
+                               double* bpart, unsigned* bcnt, cudaStream_t st);
+cudaError_t launch_apply_step(double* x, double* s, double* y, const double* dx, const double* ds,
+                              const double* dy, int64_t n, int m, const double* sc,
+                              cudaStream_t st);
+
+// scalars, sketch application, CSR -> CSC, Gram split
+cudaError_t launch_set(double* sc, int slot, double v, int* fl, int fslot, int fv, cudaStream_t st);
+cudaError_t launch_apply_W(const int32_t* hb, int ss, const double* u, int64_t n, double* wu,
+                           cudaStream_t st);
+cudaError_t csr_to_csc(const int64_t* indptr, const int32_t* indices, const void* vals,
+                       lp_dtype dt, int m, int64_t n, int64_t nnz, int64_t* colptr,
+                       int64_t* cursor, int32_t* rowidx, void* cvals, cudaStream_t st);
+int gram_split(int m, int w, int num_sms);
+
+// conversions
+cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, int m, int64_t n,
+                                 void* dst, lp_dtype ddt, int ldd, cudaStream_t st);
+cudaError_t launch_check_finite(const void* src, lp_dtype dt, int64_t count, int* flag,
+                                cudaStream_t st);
+
+}  // namespace lpk

@@ -1,0 +1,90 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads and exports every
+entry point include/lp.h declares; parameter and status plumbing work without a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(lp_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_08072_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for need in ("lp_create", "lp_normal_solve", "lp_ipm_solve", "lp_destroy", "lp_residuals",
+                 "lp_sketch", "lp_factor", "lp_normal_matvec", "lp_step", "lp_sketch_indices"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2003_08072_gb300 import _binding
+
+    assert set(_declared_functions()) <= set(_binding._SIGNATURES)
+
+
+def test_params_default_and_status_strings(lib):
+    import paper_2003_08072_gb300 as pkg
+
+    p = pkg.lp_params_default()
+    assert p.tol == 1e-8 and p.sigma == 0.5 and p.sketch_s == 4 and p.cg_rel_tol == 1e-6
+    assert ctypes.sizeof(pkg.lp_params) == 72
+    from paper_2003_08072_gb300 import _binding
+
+    assert _binding.status_str(0) == "LP_OK"
+    assert _binding.status_str(4) == "LP_ERR_BREAKDOWN"
+
+
+def test_argument_errors_need_no_device(lib):
+    """Invalid sizes are rejected before any CUDA call."""
+    import paper_2003_08072_gb300 as pkg
+    from paper_2003_08072_gb300 import _binding as B
+
+    with pytest.raises(pkg.LPError) as e:
+        B.lp_create(0, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1)
+    assert e.value.status == B.LP_ERR_ARG
+    with pytest.raises(pkg.LPError) as e:
+        B.lp_create(20, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1)
+    assert e.value.status == B.LP_ERR_ARG
+    bad = pkg.lp_params_default()
+    bad.sigma = 0.9   # Alg. 2 needs sigma < 4/5
+    with pytest.raises(pkg.LPError):
+        B.lp_create(4, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1, params=bad)
+    bad = pkg.lp_params_default()
+    bad.sketch_w = 18   # not a multiple of s = 4
+    with pytest.raises(pkg.LPError):
+        B.lp_create(4, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1, params=bad)
+    with pytest.raises(pkg.LPError):
+        B.lp_sketch_indices(0, 0, 10, 3, 16, 1, 1)   # w % s != 0
+
+
+def test_no_cpu_fallback_in_product_package():
+    """The product package never imports the oracle."""
+    pkgdir = os.path.join(ROOT, "paper_2003_08072_gb300")
+    for fn in os.listdir(pkgdir):
+        if fn.endswith(".py"):
+            src = open(os.path.join(pkgdir, fn)).read()
+            assert not re.search(r"^\s*(from|import)\s+(\.\.)?oracle", src, flags=re.M), fn
