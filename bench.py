@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark of the sketch-preconditioned IPM on one GB300 (or N replicas).
+
+One step = one LP solved to tolerance by Algorithm 2 (every step of the hot path: residuals
+and p, sketch A D W, factor, PCG, FP64 residual and correction, fused update) on the dense
+Gaussian LP with m = 1000, n = 200,000 and A in FP32 (the single-GPU configuration the
+headline metric is quoted on; A is 800 MB, larger than L2, so no flush is needed).
+
+Prints one JSON line (rank 0).  ``value`` is LPs/s over all ranks with A resident in HBM;
+``e2e`` is the same metric through the C ABI from host buffers (A, b, c copied in and x, y, s
+copied out inside the timed region); ``roofline`` is the CG product A D^2 A^T v measured live
+with CUDA events on the library's stream; ``cpu_baseline`` times the FP64 oracle on a bounded
+sample.  ``--impl reference`` runs only the oracle (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# DRAM bytes of one CG product launch from an ncu capture of the same kernel source
+# (k_coltile.cu at the recorded hash); reported only while the kernel source is unchanged.
+NCU_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None, "case": None}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=1000)
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--stream", choices=["same", "f32", "bf16", "f16"], default="same")
+    ap.add_argument("--sketch-s", type=int, default=4)
+    ap.add_argument("--cg-batch", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=20_000)
+    ap.add_argument("--cpu-sample-iters", type=int, default=4)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- distributed
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_sha1():
+    path = os.path.join(ROOT, "paper_2003_08072_gb300", "csrc", "k_coltile.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def workload_name(args):
+    return (f"dense Gaussian LP m={args.m} n={args.n} A {args.dtype.upper()} "
+            f"(feasible by construction), Algorithm 2 to scaled KKT 1e-8")
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        th = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if th:
+            return max(th)
+    except ImportError:
+        pass
+    return os.cpu_count()
+
+
+def oracle_sample(args, iters_per_lp: float):
+    """Times the FP64 oracle's Algorithm 2 for a few iterations on a column sample of the
+    workload (same generator and m, n_s columns) and converts to LP/s of the full instance:
+    per-iteration time x (n / n_s) x IPM iterations per LP."""
+    import numpy as np
+
+    import synth
+    from oracle import iipm
+
+    ns = min(args.cpu_sample_n, args.n)
+    lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64)
+    A = lp.A.astype(np.float64)
+    prm = iipm.Params(ipm_max_iter=args.cpu_sample_iters, sketch_s=args.sketch_s)
+    t0 = time.perf_counter()
+    r = iipm.ipm_solve(A, lp.b, lp.c, prm)
+    dt = time.perf_counter() - t0
+    per_iter = dt / max(r.iters, 1)
+    lp_s = 1.0 / (per_iter * (args.n / ns) * iters_per_lp)
+    sample = (f"oracle Algorithm 2 (FP64 numpy/scipy), first {r.iters} IPM iterations on the "
+              f"m={args.m}, n={ns} instance of the same generator ({dt:.1f} s); per-iteration "
+              f"time scaled by n/n_s = {args.n / ns:g} and by {iters_per_lp:g} IPM iterations "
+              f"per LP")
+    return lp_s, sample, dt
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2003_08072_gb300 as pkg
+
+    if rank == 0:
+        pkg.build.build()
+    barrier(world)
+    pkg.load(build_if_missing=False)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    np_dt = np.float32 if args.dtype == "f32" else np.float64
+    lp = synth.dense_lp(0, args.m, args.n, dtype=np_dt)
+    prm = pkg.lp_params_default()
+    prm.sketch_s = args.sketch_s
+    prm.cg_batch = args.cg_batch
+    sd = args.dtype if args.stream == "same" else args.stream
+    prm.stream_dtype = pkg.DTYPE_CODES[sd]
+    a_code = pkg.LP_F32 if args.dtype == "f32" else pkg.LP_F64
+    stream = torch.cuda.current_stream(dev)
+
+    # ---------------- device-resident runs
+    At_dev = torch.from_numpy(lp.At).to(dev)
+    b_dev = torch.from_numpy(lp.b).to(dev)
+    c_dev = torch.from_numpy(lp.c).to(dev)
+    ctx = pkg.lp_create(args.m, args.n, pkg.LP_DENSE_COLMAJOR, a_code, At_dev, None, None, 0,
+                        b_dev, c_dev, prm, stream.cuda_stream)
+    x = torch.empty(args.n, dtype=torch.float64, device=dev)
+    y = torch.empty(args.m, dtype=torch.float64, device=dev)
+    s = torch.empty(args.n, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        info = pkg.lp_ipm_solve(ctx, x, y, s)
+    pkg.lp_profile_enable(ctx, True)
+    pkg.lp_profile_read(ctx, reset=True)
+    launches0 = pkg.lp_profile_read(ctx).launches
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(pkg.lp_ipm_solve(ctx, x, y, s))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    prof = pkg.lp_profile_read(ctx)
+    launches = prof.launches - launches0
+    pkg.lp_profile_enable(ctx, False)
+    obj = float(torch.dot(c_dev, x))
+    pkg.lp_destroy(ctx)
+    del At_dev
+    torch.cuda.empty_cache()
+    t_max = max_over_ranks(elapsed, world)
+
+    # ---------------- end to end from host buffers through the C ABI
+    k_e2e = args.e2e_steps if args.e2e_steps is not None else args.steps
+    At_h = torch.from_numpy(lp.At).pin_memory()
+    b_h = torch.from_numpy(lp.b).pin_memory()
+    c_h = torch.from_numpy(lp.c).pin_memory()
+    xh = torch.empty(args.n, dtype=torch.float64).pin_memory()
+    yh = torch.empty(args.m, dtype=torch.float64).pin_memory()
+    sh = torch.empty(args.n, dtype=torch.float64).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        cx = pkg.lp_create(args.m, args.n, pkg.LP_DENSE_COLMAJOR, a_code, At_h, None, None, 0,
+                           b_h, c_h, prm, stream.cuda_stream)
+        pkg.lp_ipm_solve(cx, xh, yh, sh)
+        pkg.lp_destroy(cx)
+    torch.cuda.synchronize(dev)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world)
+    h2d = At_h.numel() * At_h.element_size() + 8 * (args.m + args.n)
+    d2h = 8 * (2 * args.n + args.m)
+
+    if rank != 0:
+        return None
+    peak, peak_kind = read_peaks()
+    mv_avg_s = prof.matvec_ms / 1e3 / max(prof.matvec_count, 1)
+    achieved = prof.matvec_bytes / mv_avg_s / 1e9 if prof.matvec_count else None
+    traffic = None
+    if NCU_TRAFFIC["source_sha1"] == kernel_sha1() and NCU_TRAFFIC["bytes_per_launch"]:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    ipm_iters = statistics.mean(i.ipm_iters for i in infos)
+    cg_total = statistics.mean(i.cg_iters_total for i in infos)
+    value = world * args.steps / t_max
+    line = {
+        "metric": "IPM LPs/s (Algorithm 2 to tolerance, dense m=1000 n=200000 FP32 LP)"
+        if (args.m, args.n, args.dtype) == (1000, 200_000, "f32") else
+        f"IPM LPs/s (Algorithm 2 to tolerance, dense m={args.m} n={args.n} {args.dtype})",
+        "value": value,
+        "unit": "LP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": sd,
+        "data": "synthetic",
+        "config": {
+            "workload": workload_name(args),
+            "m": args.m, "n": args.n, "a_dtype": args.dtype, "stream_dtype": sd,
+            "sketch": f"sparse sign s={args.sketch_s}, w=4m", "cg_rel_tol": prm.cg_rel_tol,
+            "tol": prm.tol, "sigma": prm.sigma, "gamma": prm.gamma,
+            "l2": "inputs larger than L2 (A is %.0f MB)" % (lp.At.nbytes / 1e6),
+            "parallelism": f"replicas x{world}",
+        },
+        "roofline": {
+            "kernel": "k_coltile (CG product A D^2 A^T v)",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "peak_kind": f"{peak_kind} hbm_gbs",
+            "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "bytes_per_launch": prof.matvec_bytes,
+            "avg_launch_us": 1e6 * mv_avg_s,
+            "launches": int(prof.matvec_count),
+        },
+        "e2e": {"value": world * k_e2e / e2e_t, "unit": "LP/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": k_e2e},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "ipm_iters_per_lp": ipm_iters,
+        "cg_iters_per_lp": cg_total,
+        "objective": obj,
+        "kkt": max(infos[-1].rp_rel, infos[-1].rd_rel, infos[-1].gap_rel),
+        "phase_ms_per_step": {k: v / args.steps for k, v in prof.as_dict()["phase_ms"].items()},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, sample, secs = oracle_sample(args, ipm_iters)
+        line["cpu_baseline"] = {"value": v, "unit": "LP/s", "cores": cpu_threads(),
+                                "kind": "oracle", "sample": sample}
+    else:
+        line["cpu_baseline"] = None
+    return line
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def oracle_iters_per_lp(args) -> float:
+    """IPM iterations the oracle needs for the column-sample instance (exact-solve variant,
+    cheap; the sketch variant agrees to within one iteration)."""
+    import numpy as np
+
+    import synth
+    from oracle import iipm
+
+    ns = min(args.cpu_sample_n, args.n)
+    lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64)
+    r = iipm.ipm_solve(lp.A.astype(np.float64), lp.b, lp.c, iipm.Params(), variant="exact")
+    return float(r.iters)
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle, as it stands, on the host cores: each step one bounded sample."""
+    if rank != 0:
+        return None
+    iters_per_lp = oracle_iters_per_lp(args)
+    for _ in range(args.warmup):
+        oracle_sample(args, iters_per_lp)
+    vals, secs = [], 0.0
+    sample = ""
+    for _ in range(args.steps):
+        v, sample, dt = oracle_sample(args, iters_per_lp)
+        vals.append(v)
+        secs += dt
+    value = statistics.mean(vals)
+    return {
+        "impl": "reference",
+        "metric": "IPM LPs/s (Algorithm 2 to tolerance, dense m=1000 n=200000 FP32 LP)",
+        "value": value, "unit": "LP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args), "m": args.m, "n": args.n},
+        "cpu_baseline": {"value": value, "unit": "LP/s", "cores": cpu_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "LP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -232,6 +232,38 @@ lp_status lp_step(lp_ctx* ctx, double* x, double* y, double* s, const double* rd
                   const double* dy, const double* Atdy, const double* Wu, double mu, double eta,
                   double mu0, double* dx, double* ds, double* out);
 
+/* ---------------- measurement (not part of the method) ---------------- */
+
+/* Phases timed by lp_profile_read. */
+enum {
+  LP_PH_RESIDUALS = 0,   /* Alg. 2 step (b): residual pass and p */
+  LP_PH_SKETCH = 1,      /* A D W */
+  LP_PH_FACTOR = 2,      /* Q and Q^{-1} */
+  LP_PH_PCG = 3,         /* CG iterations on A D^2 A^T (all kernels) */
+  LP_PH_RTILDE = 4,      /* FP64 residual passes r~ = A D^2 A^T dy - p */
+  LP_PH_CORRECTION = 5,  /* u = (A D W)^dagger r~ */
+  LP_PH_UPDATE = 6,      /* directions, step length, update */
+  LP_PH_COUNT = 8
+};
+
+typedef struct {
+  double phase_ms[LP_PH_COUNT];     /* device time per phase: CUDA events on the context stream */
+  int64_t phase_calls[LP_PH_COUNT];
+  double matvec_ms;                 /* summed duration of the CG product kernels that did work */
+  int64_t matvec_count;             /* number of those launches */
+  double matvec_bytes;              /* algorithmic bytes of one CG product (read of A, D^2, v) */
+  int64_t launches;                 /* kernel launches issued by the library since load (all contexts) */
+} lp_profile;
+
+/*
+ * lp_profile_enable -- on != 0 records CUDA events around each phase and around every CG
+ * product kernel of this context (adds a few microseconds per event pair); 0 stops recording.
+ */
+lp_status lp_profile_enable(lp_ctx* ctx, int32_t on);
+
+/* lp_profile_read -- copies the accumulated profile into *out (host); reset != 0 zeroes it. */
+lp_status lp_profile_read(lp_ctx* ctx, lp_profile* out, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

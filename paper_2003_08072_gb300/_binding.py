@@ -61,6 +61,27 @@ class lp_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lp_profile(ctypes.Structure):
+    _fields_ = [
+        ("phase_ms", ctypes.c_double * 8),
+        ("phase_calls", ctypes.c_int64 * 8),
+        ("matvec_ms", ctypes.c_double),
+        ("matvec_count", ctypes.c_int64),
+        ("matvec_bytes", ctypes.c_double),
+        ("launches", ctypes.c_int64),
+    ]
+
+    PHASES = ("residuals", "sketch", "factor", "pcg", "rtilde", "correction", "update", "other")
+
+    def as_dict(self):
+        return {
+            "phase_ms": {k: self.phase_ms[i] for i, k in enumerate(self.PHASES)},
+            "phase_calls": {k: int(self.phase_calls[i]) for i, k in enumerate(self.PHASES)},
+            "matvec_ms": self.matvec_ms, "matvec_count": int(self.matvec_count),
+            "matvec_bytes": self.matvec_bytes, "launches": int(self.launches),
+        }
+
+
 class LPError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{status_str(status)}: {msg}")
@@ -91,6 +112,8 @@ _SIGNATURES = {
     "lp_normal_matvec": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "lp_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _D, _D, _D, _VP, _VP,
                                _VP]),
+    "lp_profile_enable": (ctypes.c_int, [_VP, _I32]),
+    "lp_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(lp_profile), _I32]),
 }
 
 
@@ -210,3 +233,13 @@ def lp_step(ctx, x, y, s, rd, dy, Atdy, Wu, mu, eta, mu0, dx=None, ds=None):
     _check(load().lp_step(ctx, _p(x), _p(y), _p(s), _p(rd), _p(dy), _p(Atdy), _p(Wu), mu, eta,
                           mu0, _p(dx), _p(ds), ctypes.cast(out, _VP)))
     return tuple(out)
+
+
+def lp_profile_enable(ctx, on=True):
+    _check(load().lp_profile_enable(ctx, 1 if on else 0))
+
+
+def lp_profile_read(ctx, reset=False) -> lp_profile:
+    p = lp_profile()
+    _check(load().lp_profile_read(ctx, ctypes.byref(p), 1 if reset else 0))
+    return p

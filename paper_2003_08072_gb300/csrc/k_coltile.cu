@@ -177,7 +177,7 @@ int launch_t(ColArgs a, int num_sms, cudaStream_t st) {
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > a.ntiles) grid = a.ntiles;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, threads, 0, st>>>(a);
+  { note_launch(); kern<<<(unsigned)grid, threads, 0, st>>>(a); }
   return (int)grid;
 }
 

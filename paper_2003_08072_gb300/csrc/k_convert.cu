@@ -54,12 +54,12 @@ static cudaError_t conv_t(const void* src, bool rowmajor, int m, int64_t n, void
                           cudaStream_t st) {
   if (rowmajor) {
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((ldd + 31) / 32));
-    k_conv_rowmajor<TS, TD><<<grid, dim3(32, 8), 0, st>>>(src, m, n, (TD*)dst, ldd);
+    { note_launch(); k_conv_rowmajor<TS, TD><<<grid, dim3(32, 8), 0, st>>>(src, m, n, (TD*)dst, ldd); }
   } else {
     int64_t total = (int64_t)ldd * n;
     int64_t g = (total + 255) / 256;
     if (g > 65535) g = 65535;
-    k_conv_colmajor<TS, TD><<<(unsigned)g, 256, 0, st>>>(src, m, n, (TD*)dst, ldd);
+    { note_launch(); k_conv_colmajor<TS, TD><<<(unsigned)g, 256, 0, st>>>(src, m, n, (TD*)dst, ldd); }
   }
   return cudaGetLastError();
 }
@@ -100,9 +100,9 @@ cudaError_t launch_check_finite(const void* src, lp_dtype dt, int64_t count, int
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
   if (dt == LP_F64)
-    k_check_finite<double><<<(unsigned)g, 256, 0, st>>>((const double*)src, count, flag);
+    { note_launch(); k_check_finite<double><<<(unsigned)g, 256, 0, st>>>((const double*)src, count, flag); }
   else if (dt == LP_F32)
-    k_check_finite<float><<<(unsigned)g, 256, 0, st>>>((const float*)src, count, flag);
+    { note_launch(); k_check_finite<float><<<(unsigned)g, 256, 0, st>>>((const float*)src, count, flag); }
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -115,7 +115,7 @@ __global__ void k_set_scalars(double* sc, int slot, double v, int* fl, int fslot
 
 cudaError_t launch_set(double* sc, int slot, double v, int* fl, int fslot, int fv,
                        cudaStream_t st) {
-  k_set_scalars<<<1, 1, 0, st>>>(sc, slot, v, fl, fslot, fv);
+  { note_launch(); k_set_scalars<<<1, 1, 0, st>>>(sc, slot, v, fl, fslot, fv); }
   return cudaGetLastError();
 }
 
@@ -139,7 +139,7 @@ cudaError_t launch_apply_W(const int32_t* hb, int ss, const double* u, int64_t n
   int64_t g = (n + 255) / 256;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
-  k_apply_W<<<(unsigned)g, 256, 0, st>>>(hb, ss, u, n, wu);
+  { note_launch(); k_apply_W<<<(unsigned)g, 256, 0, st>>>(hb, ss, u, n, wu); }
   return cudaGetLastError();
 }
 

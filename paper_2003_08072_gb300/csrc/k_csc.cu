@@ -84,7 +84,7 @@ static int launch_csc_t(CscArgs a, int num_sms, cudaStream_t st) {
   const int64_t need = (a.n + 63) / 64;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, 512, smem, st>>>(a);
+  { note_launch(); kern<<<(unsigned)grid, 512, smem, st>>>(a); }
   return (int)grid;
 }
 
@@ -178,20 +178,20 @@ cudaError_t csr_to_csc(const int64_t* indptr, const int32_t* indices, const void
   int64_t g = (nnz + 255) / 256;
   if (g > 8192) g = 8192;
   if (g < 1) g = 1;
-  k_csr_count<<<(unsigned)g, 256, 0, st>>>(indptr, indices, m, nnz, colptr);
-  k_inclusive_scan_i64<<<1, 1024, 0, st>>>(colptr, n + 1);
+  { note_launch(); k_csr_count<<<(unsigned)g, 256, 0, st>>>(indptr, indices, m, nnz, colptr); }
+  { note_launch(); k_inclusive_scan_i64<<<1, 1024, 0, st>>>(colptr, n + 1); }
   const int rg = m < 8192 ? m : 8192;
   int64_t sg = (n + 255) / 256;
   if (sg > 8192) sg = 8192;
   if (sg < 1) sg = 1;
   if (dt == LP_F32) {
-    k_csr_scatter<float><<<rg, 256, 0, st>>>(indptr, indices, (const float*)vals, m, colptr,
-                                             cursor, rowidx, (float*)cvals);
-    k_csc_sortcols<float><<<(unsigned)sg, 256, 0, st>>>(colptr, n, rowidx, (float*)cvals);
+    { note_launch(); k_csr_scatter<float><<<rg, 256, 0, st>>>(indptr, indices, (const float*)vals, m, colptr,
+                                             cursor, rowidx, (float*)cvals); }
+    { note_launch(); k_csc_sortcols<float><<<(unsigned)sg, 256, 0, st>>>(colptr, n, rowidx, (float*)cvals); }
   } else {
-    k_csr_scatter<double><<<rg, 256, 0, st>>>(indptr, indices, (const double*)vals, m, colptr,
-                                              cursor, rowidx, (double*)cvals);
-    k_csc_sortcols<double><<<(unsigned)sg, 256, 0, st>>>(colptr, n, rowidx, (double*)cvals);
+    { note_launch(); k_csr_scatter<double><<<rg, 256, 0, st>>>(indptr, indices, (const double*)vals, m, colptr,
+                                              cursor, rowidx, (double*)cvals); }
+    { note_launch(); k_csc_sortcols<double><<<(unsigned)sg, 256, 0, st>>>(colptr, n, rowidx, (double*)cvals); }
   }
   return cudaGetLastError();
 }

@@ -99,8 +99,8 @@ cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* 
   int chunk = (w + split - 1) / split;
   chunk = (chunk + kGK - 1) / kGK * kGK;
   dim3 grid(ntiles, split);
-  k_gram_tile<<<grid, 256, 0, st>>>(G, ldg, m, w, chunk, Qsplit, ntiles);
-  k_gram_finish<<<ntiles, 256, 0, st>>>(Qsplit, split, ntiles, m, mp, Q);
+  { note_launch(); k_gram_tile<<<grid, 256, 0, st>>>(G, ldg, m, w, chunk, Qsplit, ntiles); }
+  { note_launch(); k_gram_finish<<<ntiles, 256, 0, st>>>(Qsplit, split, ntiles, m, mp, Q); }
   return cudaGetLastError();
 }
 
@@ -204,13 +204,25 @@ __global__ void __launch_bounds__(256) k_gj_update(double* __restrict__ M, int m
   }
 }
 
+// Relative diagonal shift M_ii *= (1 + eps): keeps the preconditioner positive definite when
+// the Gram matrix is numerically singular (e.g. colliding CountSketch buckets late in the IPM).
+__global__ void k_shift_diag(double* M, int mp, int m, double eps) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    M[(size_t)i * mp + i] *= (1.0 + eps);
+}
+
+cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t st) {
+  { note_launch(); k_shift_diag<<<(m + 255) / 256, 256, 0, st>>>(M, mp, m, eps); }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gj_inverse(double* M, const double* Q0, int mp, double* Pinv, double* T,
                               double* C, int* fl, cudaStream_t st) {
   const int nb = mp / kNB;
   for (int kb = 0; kb < nb; ++kb) {
-    k_gj_pivot<<<1, 256, 0, st>>>(M, Q0, mp, kb, Pinv, fl);
-    k_gj_panel<<<nb, 256, 0, st>>>(M, mp, kb, Pinv, T, C, fl);
-    k_gj_update<<<dim3(nb, nb), 256, 0, st>>>(M, mp, kb, Pinv, T, C, fl);
+    { note_launch(); k_gj_pivot<<<1, 256, 0, st>>>(M, Q0, mp, kb, Pinv, fl); }
+    { note_launch(); k_gj_panel<<<nb, 256, 0, st>>>(M, mp, kb, Pinv, T, C, fl); }
+    { note_launch(); k_gj_update<<<dim3(nb, nb), 256, 0, st>>>(M, mp, kb, Pinv, T, C, fl); }
   }
   return cudaGetLastError();
 }

@@ -47,7 +47,7 @@ cudaError_t launch_sketch_hash(uint64_t seed, int k, int64_t n, int s, int w, in
   int64_t grid = (total + 255) / 256;
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
-  k_sketch_hash<<<(unsigned)grid, 256, 0, st>>>(seed, k, n, s, w, hb, cnt, bucket_out, sign_out);
+  { note_launch(); k_sketch_hash<<<(unsigned)grid, 256, 0, st>>>(seed, k, n, s, w, hb, cnt, bucket_out, sign_out); }
   return cudaGetLastError();
 }
 
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* cnt, int w, int32_
 
 cudaError_t launch_sketch_scan(const int32_t* cnt, int w, int32_t* start, int32_t* cursor,
                                cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(cnt, w, start, cursor);
+  { note_launch(); k_scan<<<1, 1024, 0, st>>>(cnt, w, start, cursor); }
   return cudaGetLastError();
 }
 
@@ -101,7 +101,7 @@ cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, const int
   int64_t grid = (total + 255) / 256;
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
-  k_scatter<<<(unsigned)grid, 256, 0, st>>>(hb, n, s, start, cursor, list);
+  { note_launch(); k_scatter<<<(unsigned)grid, 256, 0, st>>>(hb, n, s, start, cursor, list); }
   return cudaGetLastError();
 }
 
@@ -179,10 +179,10 @@ static cudaError_t gather_dense_t(const void* A, int64_t lda, int m, int s, int 
   const int threads = ((nslices + spw - 1) / spw) * 32;
   const TA* Ap = reinterpret_cast<const TA*>(A);
   switch (spw) {
-    case 1: k_gather_dense<TA, 1><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); break;
-    case 2: k_gather_dense<TA, 2><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); break;
-    case 4: k_gather_dense<TA, 4><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); break;
-    default: k_gather_dense<TA, 8><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); break;
+    case 1: { note_launch(); k_gather_dense<TA, 1><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); } break;
+    case 2: { note_launch(); k_gather_dense<TA, 2><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); } break;
+    case 4: { note_launch(); k_gather_dense<TA, 4><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); } break;
+    default: { note_launch(); k_gather_dense<TA, 8><<<w, threads, 0, st>>>(Ap, lda, m, s, start, list, d, G, ldg); } break;
   }
   return cudaGetLastError();
 }
@@ -234,14 +234,14 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_gather_csc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-    k_gather_csc<float><<<w, 256, smem, st>>>(colptr, rowidx, (const float*)vals, m, s, start,
-                                              list, d, G, ldg);
+    { note_launch(); k_gather_csc<float><<<w, 256, smem, st>>>(colptr, rowidx, (const float*)vals, m, s, start,
+                                              list, d, G, ldg); }
   } else if (tv == LP_F64) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_gather_csc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-    k_gather_csc<double><<<w, 256, smem, st>>>(colptr, rowidx, (const double*)vals, m, s, start,
-                                               list, d, G, ldg);
+    { note_launch(); k_gather_csc<double><<<w, 256, smem, st>>>(colptr, rowidx, (const double*)vals, m, s, start,
+                                               list, d, G, ldg); }
   } else {
     return cudaErrorInvalidValue;
   }

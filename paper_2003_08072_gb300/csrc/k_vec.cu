@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(256) k_reduce(RedArgs a) {
 cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st) {
   const int grid = (a.m + 31) / 32;
   if (a.acc_f64)
-    k_reduce<double><<<grid, 256, 0, st>>>(a);
+    { note_launch(); k_reduce<double><<<grid, 256, 0, st>>>(a); }
   else
-    k_reduce<float><<<grid, 256, 0, st>>>(a);
+    { note_launch(); k_reduce<float><<<grid, 256, 0, st>>>(a); }
   return cudaGetLastError();
 }
 
@@ -116,7 +116,7 @@ static int vec_grid(int64_t n) {
 cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
                                 double* sc, double* bpart, unsigned* bcnt, double sigma,
                                 const double* c, cudaStream_t st) {
-  k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c);
+  { note_launch(); k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c); }
   return cudaGetLastError();
 }
 
@@ -131,7 +131,7 @@ __global__ void k_norm2(const double* __restrict__ v, int64_t n, double* sc, int
 
 cudaError_t launch_norm2(const double* v, int64_t n, double* sc, int slot, double* bpart,
                          unsigned* bcnt, cudaStream_t st) {
-  k_norm2<<<vec_grid(n), 256, 0, st>>>(v, n, sc, slot, bpart, bcnt);
+  { note_launch(); k_norm2<<<vec_grid(n), 256, 0, st>>>(v, n, sc, slot, bpart, bcnt); }
   return cudaGetLastError();
 }
 
@@ -206,7 +206,7 @@ cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, dou
                             cudaStream_t st) {
   SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, mode, 0.0};
   const size_t smem = (size_t)m * sizeof(double);
-  k_symv<<<(m + 7) / 8, 256, smem, st>>>(a);
+  { note_launch(); k_symv<<<(m + 7) / 8, 256, smem, st>>>(a); }
   return cudaGetLastError();
 }
 
@@ -215,7 +215,7 @@ cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, do
                              cudaStream_t st) {
   SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, SYMV_CG_INIT, rel_tol * rel_tol};
   const size_t smem = (size_t)m * sizeof(double);
-  k_symv<<<(m + 7) / 8, 256, smem, st>>>(a);
+  { note_launch(); k_symv<<<(m + 7) / 8, 256, smem, st>>>(a); }
   return cudaGetLastError();
 }
 
@@ -241,7 +241,7 @@ __global__ void k_cg_axpy(double* dy, double* r, const double* d, const double* 
 
 cudaError_t launch_cg_axpy(double* dy, double* r, const double* d, const double* q, int m,
                            const double* sc, const int* fl, cudaStream_t st) {
-  k_cg_axpy<<<(m + 255) / 256, 256, 0, st>>>(dy, r, d, q, m, sc, fl);
+  { note_launch(); k_cg_axpy<<<(m + 255) / 256, 256, 0, st>>>(dy, r, d, q, m, sc, fl); }
   return cudaGetLastError();
 }
 
@@ -254,7 +254,7 @@ __global__ void k_cg_dir(double* d, const double* z, int m, const double* sc, co
 
 cudaError_t launch_cg_dir(double* d, const double* z, int m, const double* sc, const int* fl,
                           cudaStream_t st) {
-  k_cg_dir<<<(m + 255) / 256, 256, 0, st>>>(d, z, m, sc, fl);
+  { note_launch(); k_cg_dir<<<(m + 255) / 256, 256, 0, st>>>(d, z, m, sc, fl); }
   return cudaGetLastError();
 }
 
@@ -273,7 +273,7 @@ __global__ void k_vec_ops(int op, double* a, const double* b, const double* c, i
 cudaError_t launch_vec_ops(int op, double* a, const double* b, const double* c, int m,
                            const double* sc, cudaStream_t st) {
   (void)sc;
-  k_vec_ops<<<vec_grid(m), 256, 0, st>>>(op, a, b, c, m);
+  { note_launch(); k_vec_ops<<<vec_grid(m), 256, 0, st>>>(op, a, b, c, m); }
   return cudaGetLastError();
 }
 
@@ -333,8 +333,8 @@ cudaError_t launch_update_dirs(const double* x, const double* s, const double* d
                                const double* u, int64_t n, double* wu, double* dx, double* ds,
                                int wu_given, double* sc, double* bpart, unsigned* bcnt,
                                cudaStream_t st) {
-  k_update_dirs<<<vec_grid(n), 256, 0, st>>>(x, s, d2, d, rd, t, hb, ss, u, n, wu, dx, ds,
-                                             wu_given, sc, bpart, bcnt);
+  { note_launch(); k_update_dirs<<<vec_grid(n), 256, 0, st>>>(x, s, d2, d, rd, t, hb, ss, u, n, wu, dx, ds,
+                                             wu_given, sc, bpart, bcnt); }
   return cudaGetLastError();
 }
 
@@ -405,7 +405,7 @@ __global__ void k_step_length(const double* __restrict__ x, const double* __rest
 cudaError_t launch_step_length(const double* x, const double* s, const double* dx,
                                const double* ds, int64_t n, double gamma, double* sc,
                                double* bpart, unsigned* bcnt, cudaStream_t st) {
-  k_step_length<<<vec_grid(n), 256, 0, st>>>(x, s, dx, ds, n, gamma, sc, bpart, bcnt);
+  { note_launch(); k_step_length<<<vec_grid(n), 256, 0, st>>>(x, s, dx, ds, n, gamma, sc, bpart, bcnt); }
   return cudaGetLastError();
 }
 
@@ -424,7 +424,7 @@ __global__ void k_apply_step(double* x, double* s, double* y, const double* dx, 
 cudaError_t launch_apply_step(double* x, double* s, double* y, const double* dx, const double* ds,
                               const double* dy, int64_t n, int m, const double* sc,
                               cudaStream_t st) {
-  k_apply_step<<<vec_grid(n), 256, 0, st>>>(x, s, y, dx, ds, dy, n, m, sc);
+  { note_launch(); k_apply_step<<<vec_grid(n), 256, 0, st>>>(x, s, y, dx, ds, dy, n, m, sc); }
   return cudaGetLastError();
 }
 

@@ -10,6 +10,8 @@
 
 using namespace lpk;
 
+std::atomic<long long> lpk::g_launches{0};
+
 static thread_local std::string g_err;
 
 void lp_set_error(const std::string& msg) { g_err = msg; }
@@ -128,6 +130,15 @@ extern "C" void lp_destroy(lp_ctx* c) {
   for (void* p : bufs) dfree(p);
   if (c->sc_h) cudaFreeHost(c->sc_h);
   if (c->fl_h) cudaFreeHost(c->fl_h);
+  for (auto& pr : c->ev_pending) {
+    if (pr.a) cudaEventDestroy(pr.a);
+    if (pr.b) cudaEventDestroy(pr.b);
+  }
+  for (auto& pr : c->mv_pending) {
+    if (pr.a) cudaEventDestroy(pr.a);
+    if (pr.b) cudaEventDestroy(pr.b);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -178,10 +189,78 @@ static lp_status alloc_workspace(lp_ctx* c) {
   return LP_OK;
 }
 
+// ---- profiling: event pairs recorded on the context stream, harvested after a sync --------
+static cudaEvent_t ev_get(lp_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+static void ev_put(lp_ctx* c, cudaEvent_t e) {
+  if (e) c->ev_pool.push_back(e);
+}
+
+// Harvests finished phase events (the stream has been synchronized).
+static void prof_harvest(lp_ctx* c) {
+  for (auto& pr : c->ev_pending) {
+    float ms = 0.f;
+    if (pr.a && pr.b && cudaEventElapsedTime(&ms, pr.a, pr.b) == cudaSuccess &&
+        pr.phase >= 0 && pr.phase < LP_PH_COUNT) {
+      c->prof.phase_ms[pr.phase] += ms;
+      c->prof.phase_calls[pr.phase] += 1;
+    }
+    cudaGetLastError();
+    ev_put(c, pr.a);
+    ev_put(c, pr.b);
+  }
+  c->ev_pending.clear();
+}
+
+// Harvests the CG product events of one batch: the first `real` launches did work, the rest
+// found the CG finished and returned at once.
+static void prof_harvest_mv(lp_ctx* c, int real) {
+  for (size_t i = 0; i < c->mv_pending.size(); ++i) {
+    auto& pr = c->mv_pending[i];
+    float ms = 0.f;
+    if ((int)i < real && pr.a && pr.b && cudaEventElapsedTime(&ms, pr.a, pr.b) == cudaSuccess) {
+      c->prof.matvec_ms += ms;
+      c->prof.matvec_count += 1;
+    }
+    cudaGetLastError();
+    ev_put(c, pr.a);
+    ev_put(c, pr.b);
+  }
+  c->mv_pending.clear();
+}
+
+struct PhaseScope {
+  lp_ctx* c;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(lp_ctx* cc, int ph) : c(cc), phase(ph) {
+    if (c->prof_on && (a = ev_get(c))) cudaEventRecord(a, c->st);
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    cudaEvent_t b = ev_get(c);
+    if (b) cudaEventRecord(b, c->st);
+    c->ev_pending.push_back({phase, a, b});
+  }
+};
+
 static lp_status sync_scalars(lp_ctx* c) {
   LP_CU(cudaMemcpyAsync(c->sc_h, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   LP_CU(cudaMemcpyAsync(c->fl_h, c->fl, FL_COUNT * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   LP_CU(cudaStreamSynchronize(c->st));
+  if (!c->ev_pending.empty()) prof_harvest(c);
   return LP_OK;
 }
 
@@ -356,9 +435,11 @@ extern "C" lp_status lp_set_params(lp_ctx* c, const lp_params* prm) {
 // precise: master copy with FP64 accumulation; else the streamed copy.
 static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const double* w, double* t,
                              int red_mode, double* out, const double* p0, int skip_if_done,
-                             int* nblk_out = nullptr) {
+                             bool record_mv = false) {
   int nblk;
   bool acc64;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (record_mv && c->prof_on && (ea = ev_get(c))) cudaEventRecord(ea, c->st);
   if (!c->sparse) {
     ColArgs a{};
     const lp_dtype ta = precise ? c->a_dtype : c->s_dtype;
@@ -391,6 +472,10 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     acc64 = precise || tv == LP_F64;
     nblk = launch_csc(tv, acc64, MODE_NORMAL, a, c->num_sms, c->st);
   }
+  if (ea) {
+    if ((eb = ev_get(c))) cudaEventRecord(eb, c->st);
+    c->mv_pending.push_back({-1, ea, eb});
+  }
   if (nblk < 0) return fail(LP_ERR_ARG, "unsupported shape for the matrix pass");
   LP_CU(cudaGetLastError());
   RedArgs r{};
@@ -409,13 +494,13 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
   r.bcnt = c->bcnt;
   r.skip_if_done = skip_if_done;
   LP_CU(launch_reduce(r, c->st));
-  if (nblk_out) *nblk_out = nblk;
   return LP_OK;
 }
 
-// Product with the sketch: out = G G^T v - p0 (red_mode MINUS_P) and u = G^T v.
+// Product with the sketch Q v = G G^T v in FP64, u = G^T v (optional), reduced by red_mode:
+// RED_MINUS_P: out = Q v - p0;  RED_PLAIN: out = Q v;  RED_CG_Q: out = q = Q v and d^T q.
 static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* u, double* out,
-                           const double* p0) {
+                           const double* p0, int red_mode, int skip_if_done) {
   ColArgs a{};
   a.A = G;
   a.lda = c->ldg;
@@ -426,11 +511,11 @@ static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* 
   a.colout = u;
   a.part = c->part;
   a.fl = c->fl;
-  a.skip_if_done = 0;
+  a.skip_if_done = skip_if_done;
   const int nblk = launch_coltile(LP_F64, true, MODE_NORMAL, a, c->num_sms, c->st);
   if (nblk < 0) return fail(LP_ERR_ARG, "unsupported shape for the sketch pass");
   RedArgs r{};
-  r.mode = p0 ? RED_MINUS_P : RED_PLAIN;
+  r.mode = red_mode;
   r.part = c->part;
   r.nblk = nblk;
   r.nout = 1;
@@ -438,10 +523,12 @@ static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* 
   r.acc_f64 = true;
   r.out0 = out;
   r.p0 = p0;
+  r.dvec = v;
   r.sc = c->sc;
   r.fl = c->fl;
   r.bpart = c->bpart;
   r.bcnt = c->bcnt;
+  r.skip_if_done = skip_if_done;
   LP_CU(launch_reduce(r, c->st));
   return LP_OK;
 }
@@ -449,6 +536,7 @@ static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* 
 // Alg. 2 step (b): d2, d, mu from (x, s); r_p, r_d, p in one pass; ||r_p||^2, ||r_d||^2.
 static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, const double* s,
                                double sigma, double* rp, double* rd, double* p) {
+  PhaseScope ps(c, LP_PH_RESIDUALS);
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, sigma, c->c, c->st));
   int nblk;
   if (!c->sparse) {
@@ -506,6 +594,7 @@ static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, cons
 
 // Alg. 1 step 1 / Alg. 2 step (a): G = A D W(seed, k).
 static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
+  PhaseScope ps(c, LP_PH_SKETCH);
   LP_CU(cudaMemsetAsync(c->cnt, 0, (c->w + 1) * sizeof(int32_t), c->st));
   LP_CU(launch_sketch_hash(c->prm.seed, k, c->n, c->ss, c->w, c->hb, c->cnt, nullptr, nullptr, c->st));
   LP_CU(launch_sketch_scan(c->cnt, c->w, c->start, c->cursor, c->st));
@@ -520,41 +609,61 @@ static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
   return LP_OK;
 }
 
-// Alg. 1 step 2: Q = G G^T, M = Q^{-1}.
-static lp_status run_factor(lp_ctx* c, const double* G) {
-  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
+// Alg. 1 step 2: Q = G G^T, M = Q^{-1}.  With allow_shift, a lost pivot (Q numerically
+// singular) is retried with M = (Q + eps diag(Q))^{-1}, eps = 1e-10, 1e-8, ..., 1e-4: M is
+// then only a preconditioner, and (A D W)^dagger is applied by PCG on Q itself.
+static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
+  PhaseScope ps(c, LP_PH_FACTOR);
   LP_CU(launch_gram(G, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
-  LP_CU(cudaMemcpyAsync(c->M, c->Q, (size_t)c->mp * c->mp * sizeof(double),
-                        cudaMemcpyDeviceToDevice, c->st));
-  LP_CU(launch_gj_inverse(c->M, c->Q, c->mp, c->Pinv, c->T, c->C, c->fl, c->st));
-  LP_TRY(sync_scalars(c));
-  if (c->fl_h[FL_BREAK])
-    return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (non-positive pivot)");
+  double eps = 0.0;
+  for (;;) {
+    LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
+    LP_CU(cudaMemcpyAsync(c->M, c->Q, (size_t)c->mp * c->mp * sizeof(double),
+                          cudaMemcpyDeviceToDevice, c->st));
+    if (eps > 0.0) LP_CU(launch_shift_diag(c->M, c->mp, c->m, eps, c->st));
+    LP_CU(launch_gj_inverse(c->M, c->Q, c->mp, c->Pinv, c->T, c->C, c->fl, c->st));
+    LP_TRY(sync_scalars(c));
+    if (!c->fl_h[FL_BREAK]) break;
+    eps = eps > 0.0 ? eps * 100.0 : 1e-10;
+    if (!allow_shift || eps > 1e-4)
+      return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (pivot lost in the inverse)");
+  }
+  c->shift = eps;
   return LP_OK;
 }
 
-// PCG (Alg. 1 step 3) on (A D^2 A^T) delta = rhs with preconditioner Q, from delta = 0.
-// Stops when rho_j <= min(rel^2 rho_0, abs_thr^2) or after cg_max_iter products.
-static lp_status run_pcg(lp_ctx* c, const double* rhs, double* delta, double abs_thr,
-                         int* iters, double* rho0_out, double* rho_out) {
+// PCG from delta = 0 with preconditioner M = Q^{-1} (Alg. 1 step 3), stopping when
+// rho_j = r_j^T M r_j <= min(rel^2 rho_0, abs_thr^2) or after max_iter products.
+//   op 0: (A D^2 A^T) delta = rhs with A streamed in the context's stream dtype;
+//   op 1: (G G^T) delta = rhs in FP64 through the sketch G (for (A D W)^dagger).
+static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, double rel_tol,
+                         double abs_thr, int max_iter, int* iters, double* rho0_out,
+                         double* rho_out) {
+  PhaseScope ps(c, op == 0 ? LP_PH_PCG : LP_PH_CORRECTION);
   const int m = c->m;
   LP_CU(launch_vec_ops(VOP_ZERO, delta, nullptr, nullptr, m, nullptr, c->st));
   LP_CU(launch_vec_ops(VOP_COPY, c->r, rhs, nullptr, m, nullptr, c->st));
   const double thr2 = isfinite(abs_thr) ? abs_thr * abs_thr : INFINITY;
-  LP_CU(launch_set(c->sc, SC_THR2, thr2, c->fl, FL_MAXIT, c->prm.cg_max_iter, c->st));
+  LP_CU(launch_set(c->sc, SC_THR2, thr2, c->fl, FL_MAXIT, max_iter, c->st));
   LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_NUMERIC, 0, c->st));
-  LP_CU(launch_symv_init(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt,
-                         c->prm.cg_rel_tol, c->st));
+  LP_CU(launch_symv_init(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt, rel_tol,
+                         c->st));
   LP_CU(launch_vec_ops(VOP_COPY, c->dd, c->z, nullptr, m, nullptr, c->st));
+  int done_before = 0;
   for (;;) {
     for (int b = 0; b < c->prm.cg_batch; ++b) {
-      LP_TRY(pass_normal(c, false, c->dd, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1));
+      if (op == 0)
+        LP_TRY(pass_normal(c, false, c->dd, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1, true));
+      else
+        LP_TRY(pass_gram(c, c->G, c->dd, nullptr, c->q, nullptr, RED_CG_Q, 1));
       LP_CU(launch_cg_axpy(delta, c->r, c->dd, c->q, m, c->sc, c->fl, c->st));
       LP_CU(launch_symv_dot(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt,
                             SYMV_CG_STEP, c->st));
       LP_CU(launch_cg_dir(c->dd, c->z, m, c->sc, c->fl, c->st));
     }
     LP_TRY(sync_scalars(c));
+    if (!c->mv_pending.empty()) prof_harvest_mv(c, c->fl_h[FL_ITERS] - done_before);
+    done_before = c->fl_h[FL_ITERS];
     if (c->fl_h[FL_DONE]) break;
   }
   *iters = c->fl_h[FL_ITERS];
@@ -576,30 +685,35 @@ struct SolveOut {
 static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, SolveOut* so) {
   const int m = c->m;
   LP_TRY(run_sketch(c, c->d, k, c->G));
-  LP_TRY(run_factor(c, c->G));
+  LP_TRY(run_factor(c, c->G, true));
   double abs_thr = INFINITY;
   if (c->prm.cg_theory_rule)
     abs_thr = c->prm.gamma * c->prm.sigma * sqrt(mu) / (4.0 * sqrt((double)c->n));
-  const bool lowprec = c->s_dtype != c->a_dtype;
+  const bool lowprec = c->s_dtype != LP_F64;   // CG products accumulate in FP32
   double rho0 = 0.0, target2 = 0.0;
   int total_it = 0, outer = 0;
   for (;;) {
     int it = 0;
     double r0 = 0.0, rl = 0.0;
     if (outer == 0) {
-      LP_TRY(run_pcg(c, p, c->dyacc, abs_thr, &it, &r0, &rl));
+      LP_TRY(run_pcg(c, 0, p, c->dyacc, c->prm.cg_rel_tol, abs_thr, c->prm.cg_max_iter, &it,
+                     &r0, &rl));
       rho0 = r0;
       target2 = std::min(c->prm.cg_rel_tol * c->prm.cg_rel_tol * rho0,
                          isfinite(abs_thr) ? abs_thr * abs_thr : INFINITY);
     } else {
       // refinement: solve (A D^2 A^T) delta = -r~ and add it to dy
       LP_CU(launch_vec_ops(VOP_NEG, c->rhs, c->rtil, nullptr, m, nullptr, c->st));
-      LP_TRY(run_pcg(c, c->rhs, c->dy, abs_thr, &it, &r0, &rl));
+      LP_TRY(run_pcg(c, 0, c->rhs, c->dy, c->prm.cg_rel_tol, abs_thr, c->prm.cg_max_iter, &it,
+                     &r0, &rl));
       LP_CU(launch_vec_ops(VOP_ADD, c->dyacc, c->dyacc, c->dy, m, nullptr, c->st));
     }
     total_it += it;
     // r~ = A D^2 A^T dy - p in FP64 from the input-precision A, with t = A^T dy
-    LP_TRY(pass_normal(c, true, c->dyacc, c->d2, c->t, RED_MINUS_P, c->rtil, p, 0));
+    {
+      PhaseScope ps(c, LP_PH_RTILDE);
+      LP_TRY(pass_normal(c, true, c->dyacc, c->d2, c->t, RED_MINUS_P, c->rtil, p, 0));
+    }
     // ||f||^2 = r~^T Q^{-1} r~; qhat = Q^{-1} r~ starts the correction
     LP_CU(launch_symv_dot(c->M, c->mp, m, c->rtil, c->qhat, c->sc, c->fl, c->bpart, c->bcnt,
                           SYMV_F2, c->st));
@@ -611,21 +725,14 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
     ++outer;
   }
   so->cg_iters = total_it;
-  // u = (A D W)^T Q^{-1} r~, refining Q^{-1} r~ against Q = G G^T in FP64
-  double prev = INFINITY;
+  // u = (A D W)^dagger r~ = (A D W)^T q with Q q = r~ (Eq. compv, full row rank): PCG on
+  // Q = G G^T in FP64 with preconditioner M, then u = G^T q and the residual G u - r~.
   int steps = 0;
-  for (;;) {
-    LP_TRY(pass_gram(c, c->G, c->qhat, c->u, c->res, c->rtil));   // res = G G^T qhat - r~
-    LP_CU(launch_norm2(c->res, m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
-    LP_TRY(sync_scalars(c));
-    const double nr = sqrt(c->sc_h[SC_RES2]);
-    if (!isfinite(nr)) return fail(LP_ERR_NUMERIC, "non-finite correction residual");
-    if (nr == 0.0 || nr >= 0.5 * prev || steps >= c->prm.refine_max) break;
-    LP_CU(launch_symv_dot(c->M, c->mp, m, c->res, c->tm, c->sc, c->fl, c->bpart, c->bcnt,
-                          SYMV_PLAIN, c->st));
-    LP_CU(launch_vec_ops(VOP_SUB, c->qhat, c->qhat, c->tm, m, nullptr, c->st));
-    prev = nr;
-    ++steps;
+  LP_TRY(run_pcg(c, 1, c->rtil, c->qhat, 1e-13, INFINITY, std::max(50, c->prm.refine_max), &steps,
+                 nullptr, nullptr));
+  {
+    PhaseScope ps(c, LP_PH_CORRECTION);
+    LP_TRY(pass_gram(c, c->G, c->qhat, c->u, c->res, c->rtil, RED_MINUS_P, 0));
   }
   so->refine = steps + outer;
   return LP_OK;
@@ -635,6 +742,7 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
 static lp_status run_step(lp_ctx* c, double* x, double* y, double* s, const double* rd,
                           const double* dy, const double* t, const double* wu_given, double eta,
                           double mu0, double* dx, double* ds) {
+  PhaseScope ps(c, LP_PH_UPDATE);
   LP_CU(launch_set(c->sc, SC_ETA, eta, nullptr, 0, 0, c->st));
   LP_CU(launch_set(c->sc, SC_MU0, mu0, nullptr, 0, 0, c->st));
   double* wu = wu_given ? const_cast<double*>(wu_given) : c->wu;
@@ -796,7 +904,7 @@ extern "C" lp_status lp_factor(lp_ctx* c, const double* G, double* Q, double* Mi
   if (!c || !G) return fail(LP_ERR_ARG, "lp_factor: NULL argument");
   LP_CU(cudaMemcpy2DAsync(c->G, c->ldg * sizeof(double), G, c->m * sizeof(double),
                           c->m * sizeof(double), c->w, cudaMemcpyDefault, c->st));
-  LP_TRY(run_factor(c, c->G));
+  LP_TRY(run_factor(c, c->G, false));
   const size_t row = c->m * sizeof(double), pitch = c->mp * sizeof(double);
   if (Q) LP_CU(cudaMemcpy2DAsync(Q, row, c->Q, pitch, row, c->m, cudaMemcpyDefault, c->st));
   if (Minv) LP_CU(cudaMemcpy2DAsync(Minv, row, c->M, pitch, row, c->m, cudaMemcpyDefault, c->st));
@@ -835,6 +943,33 @@ extern "C" lp_status lp_step(lp_ctx* c, double* x, double* y, double* s, const d
     out[1] = c->sc_h[SC_STEP];
     out[2] = c->sc_h[SC_B];
     out[3] = c->sc_h[SC_C];
+  }
+  return LP_OK;
+}
+
+extern "C" lp_status lp_profile_enable(lp_ctx* c, int32_t on) {
+  if (!c) return fail(LP_ERR_ARG, "lp_profile_enable: NULL");
+  c->prof_on = on != 0;
+  return LP_OK;
+}
+
+extern "C" lp_status lp_profile_read(lp_ctx* c, lp_profile* out, int32_t reset) {
+  if (!c || !out) return fail(LP_ERR_ARG, "lp_profile_read: NULL");
+  LP_CU(cudaStreamSynchronize(c->st));
+  if (!c->ev_pending.empty()) prof_harvest(c);
+  if (!c->sparse) {
+    c->prof.matvec_bytes = (double)c->m * (double)c->n * (double)dtype_size(c->s_dtype) +
+                           8.0 * (double)c->n + 8.0 * c->m;
+  } else {
+    c->prof.matvec_bytes = (double)c->nnz * (dtype_size(c->s_dtype) + 4.0) + 8.0 * (c->n + 1) +
+                           8.0 * (double)c->n + 8.0 * c->m;
+  }
+  c->prof.launches = g_launches.load();
+  *out = c->prof;
+  if (reset) {
+    lp_profile z{};
+    z.matvec_bytes = c->prof.matvec_bytes;
+    c->prof = z;
   }
   return LP_OK;
 }

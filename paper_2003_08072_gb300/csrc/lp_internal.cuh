@@ -6,7 +6,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
+#include <vector>
 
 #include "../../include/lp.h"
 
@@ -48,6 +50,9 @@ enum Flag {
   FL_MAXIT,      // CG iteration cap of the current solve
   FL_COUNT = 8
 };
+
+extern std::atomic<long long> g_launches;   // kernel launches issued (lp_api.cu)
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int kNB = 32;          // block size of the Gauss-Jordan inverse
 constexpr int kMaxRedBlocks = 1024;
@@ -116,6 +121,7 @@ struct lp_ctx {
   double* C = nullptr;         // mp x kNB
   double* Qsplit = nullptr;    // split-k partials of the Gram product
   int qsplit = 1;
+  double shift = 0.0;          // relative diagonal shift used by the last factorization
 
   // scalars
   double* sc = nullptr;        // device SC_COUNT
@@ -124,6 +130,17 @@ struct lp_ctx {
   unsigned* bcnt = nullptr;    // last-block counters (16)
   double* sc_h = nullptr;      // pinned host mirror of sc
   int* fl_h = nullptr;         // pinned host mirror of fl
+
+  // profiling (CUDA events on st)
+  struct EvPair {
+    int phase;                 // LP_PH_* or -1 for a CG product
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<EvPair> ev_pending;
+  std::vector<EvPair> mv_pending;   // CG product launches of the current batch
+  lp_profile prof{};
 };
 
 // ---------------------------------------------------------------------------------------
@@ -232,6 +249,7 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
 // factor
 cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* Q, double* Qsplit,
                         int split, cudaStream_t st);
+cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t st);
 cudaError_t launch_gj_inverse(double* M, const double* Q0, int mp, double* Pinv, double* T,
                               double* C, int* fl, cudaStream_t st);
 
