@@ -30,7 +30,10 @@ if ROOT not in sys.path:
 
 # DRAM bytes of one CG product launch from an ncu capture of the same kernel source
 # (k_coltile.cu at the recorded hash); reported only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None, "case": None}
+NCU_TRAFFIC = {"source_sha1": "bf67889fc014d48c8dc7e02a00e34c6a2e1b3c2a",
+               "bytes_per_launch": 804.47e6,
+               "case": "dense m=1000 n=200000 FP32, ncu --set full (profiles/k_coltile_cg_product_"
+                       "dense_m1000_n200000_f32.md)"}
 
 
 def parse_args():
