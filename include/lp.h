@@ -232,6 +232,31 @@ lp_status lp_step(lp_ctx* ctx, double* x, double* y, double* s, const double* rd
                   const double* dy, const double* Atdy, const double* Wu, double mu, double eta,
                   double mu0, double* dx, double* ds, double* out);
 
+/*
+ * lp_normal_matvec_noalloc -- y = A D^2 A^T v (and t = A^T v) without a context and without
+ * allocating any device memory.  The paper has no counterpart: this entry point exists for
+ * callers that must not allocate, e.g. code running under a framework that owns every byte
+ * of device memory through its own pool, or a latency-critical loop that cannot afford the
+ * implicit device synchronisation of cudaMalloc / cudaFree.  The caller passes inputs and
+ * outputs; the per-CTA partial sums live in one 4 MiB file-scope __device__ array of the
+ * library, which every GPU that loads the library holds until the process exits.
+ *   A      : device, column-major m x n with leading dimension lda (lda >= m), 16-byte aligned,
+ *            lda * element size a multiple of 16 bytes.
+ *   a_dtype: LP_F64 (FP64 accumulation) or LP_F32 / LP_BF16 / LP_F16 (FP32 accumulation).
+ *   d2     : device n float64 (D^2).   v: device m float64.   y: device m float64 output.
+ *   t      : device n float64 output or NULL.
+ *   stream : cudaStream_t the two kernels are enqueued on.  Asynchronous.
+ * Limit: m <= min(8192, 4 MiB / (accumulator bytes x SM count)), i.e. m <= 3449 for LP_F64 and
+ * m <= 6898 otherwise on a 152-SM GB300; larger m returns LP_ERR_ARG with the limit in
+ * lp_last_error().  The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.  All calls share the
+ * one array and each overwrites it completely, so calls whose kernels overlap on the GPU (two
+ * streams, two threads) race and must be serialised by the caller.
+ */
+lp_status lp_normal_matvec_noalloc(const void* A, lp_dtype a_dtype, int32_t m, int64_t n,
+                                   int64_t lda, const double* d2, const double* v, double* y,
+                                   double* t, void* stream);
+
 /* ---------------- measurement (not part of the method) ---------------- */
 
 /* Phases timed by lp_profile_read. */

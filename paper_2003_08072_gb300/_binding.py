@@ -112,6 +112,8 @@ _SIGNATURES = {
     "lp_normal_matvec": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "lp_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _D, _D, _D, _VP, _VP,
                                _VP]),
+    "lp_normal_matvec_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _I32, _I64, _I64, _VP, _VP,
+                                                _VP, _VP, _VP]),
     "lp_profile_enable": (ctypes.c_int, [_VP, _I32]),
     "lp_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(lp_profile), _I32]),
 }
@@ -243,3 +245,9 @@ def lp_profile_read(ctx, reset=False) -> lp_profile:
     p = lp_profile()
     _check(load().lp_profile_read(ctx, ctypes.byref(p), 1 if reset else 0))
     return p
+
+
+def lp_normal_matvec_noalloc(A, a_dtype, m, n, lda, d2, v, y, t=None, stream=None):
+    """Context-free A D^2 A^T v that allocates nothing (scratch in a static device array)."""
+    _check(load().lp_normal_matvec_noalloc(_p(A), a_dtype, m, n, lda, _p(d2), _p(v), _p(y),
+                                           _p(t), _p(stream)))

@@ -207,3 +207,61 @@ int launch_coltile(lp_dtype ta, bool acc_f64, int mode, ColArgs a, int num_sms, 
 }
 
 }  // namespace lpk
+
+namespace lpk {
+
+// Same kernel selection as launch_coltile (MODE_NORMAL, accumulator of the streamed type) with
+// the grid limited to max_grid CTAs, for callers whose partial buffer has a fixed capacity.
+namespace {
+template <typename TA, typename ACC>
+int launch_capped_t(ColArgs a, int num_sms, int max_grid, cudaStream_t st) {
+  constexpr int VEC = VecN<TA>::N;
+  const int nslices = (a.m + 32 * VEC - 1) / (32 * VEC);
+  int spw = 1;
+  while ((nslices + spw - 1) / spw > 16) spw *= 2;
+  if (spw > 8) return -1;
+  const int threads = ((nslices + spw - 1) / spw) * 32;
+  constexpr bool wide = VEC * sizeof(ACC) > 16;
+  const int tile = std::max(2, (wide ? 8 : 16) / spw);
+  a.ntiles = (a.n + tile - 1) / tile;
+  void (*kern)(ColArgs) = nullptr;
+  if constexpr (wide) {
+    switch (spw) {
+      case 1: kern = k_coltile<TA, ACC, 1, 8, MODE_NORMAL>; break;
+      case 2: kern = k_coltile<TA, ACC, 2, 4, MODE_NORMAL>; break;
+      case 4: kern = k_coltile<TA, ACC, 4, 2, MODE_NORMAL>; break;
+      default: kern = k_coltile<TA, ACC, 8, 2, MODE_NORMAL>; break;
+    }
+  } else {
+    switch (spw) {
+      case 1: kern = k_coltile<TA, ACC, 1, 16, MODE_NORMAL>; break;
+      case 2: kern = k_coltile<TA, ACC, 2, 8, MODE_NORMAL>; break;
+      case 4: kern = k_coltile<TA, ACC, 4, 4, MODE_NORMAL>; break;
+      default: kern = k_coltile<TA, ACC, 8, 2, MODE_NORMAL>; break;
+    }
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  if (per_sm > 8) per_sm = 8;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  if (grid > max_grid) grid = max_grid;
+  if (grid > a.ntiles) grid = a.ntiles;
+  if (grid < 1) grid = 1;
+  { note_launch(); kern<<<(unsigned)grid, threads, 0, st>>>(a); }
+  return (int)grid;
+}
+}  // namespace
+
+int launch_coltile_capped(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t st) {
+  switch (ta) {
+    case LP_F64: return launch_capped_t<double, double>(a, num_sms, max_grid, st);
+    case LP_F32: return launch_capped_t<float, float>(a, num_sms, max_grid, st);
+    case LP_BF16: return launch_capped_t<__nv_bfloat16, float>(a, num_sms, max_grid, st);
+    case LP_F16: return launch_capped_t<__half, float>(a, num_sms, max_grid, st);
+  }
+  return -1;
+}
+
+}  // namespace lpk
