@@ -86,6 +86,7 @@ typedef struct {
   double f_norm;           /* ||f^(t)|| of the last CG solve (Sec. 3) */
   double v_norm;           /* ||v|| of the last correction vector (Eq. compv) */
   int32_t status;          /* lp_status of the solve */
+  double f_target;         /* CG target of the last solve: min(cg_rel_tol ||f^(0)||, gamma sigma sqrt(mu)/(4 sqrt(n))) */
 } lp_info;
 
 /* Fills *prm with the defaults listed above.  LP_ERR_ARG if prm is NULL. */

@@ -55,6 +55,7 @@ class lp_info(ctypes.Structure):
         ("f_norm", ctypes.c_double),
         ("v_norm", ctypes.c_double),
         ("status", ctypes.c_int32),
+        ("f_target", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -6,9 +6,8 @@
 // product over the whole GPU instead of two sequential triangular solves.
 //   1. Gram product G G^T in FP64, lower 64x64 tiles, split along w for parallelism, then
 //      summed and mirrored into a full row-major mp x mp matrix (identity on the padding).
-//   2. In-place blocked Gauss-Jordan inversion with 32 x 32 pivot blocks.  Q is symmetric
-//      positive definite when rank(A D W) = m (Lemma 4.1), so every pivot block is SPD and no
-//      pivoting is needed; a non-positive pivot flags a rank-deficient sketch.
+//   2. Q^{-1} = L^{-T} L^{-1} from a blocked Cholesky factor Q = L L^T (Q is symmetric positive
+//      definite when rank(A D W) = m, Lemma 4.1); a lost pivot flags a numerically singular Q.
 #include "dev_util.cuh"
 
 namespace lpk {
@@ -104,103 +103,225 @@ cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* 
   return cudaGetLastError();
 }
 
-// ---- blocked Gauss-Jordan inversion, pivot block kb --------------------------------------
+// ---- Q^{-1} through a blocked Cholesky factor -------------------------------------------
+//
+// Q = L L^T (right-looking, 32 x 32 blocks) and X = L^{-1} are computed in one left-to-right
+// sweep over the block columns k:
+//   panel : L_ik = A_ik X_kk^T (i > k)          and  X_kj <- X_kk X_kj (j < k)
+//   update: A_ij -= L_ik L_jk^T (k < j <= i)    and  X_ij -= L_ik X_kj (i > k, j <= k)
+// and the CTA that finishes the update of the next diagonal block (scheduled first) factors
+// it and inverts its triangle in shared memory.  Finally M = X^T X = Q^{-1}, mirrored into
+// full storage.  Unlike Gauss-Jordan elimination on Q itself this keeps the error of M near
+// kappa(Q) u (backward-stable Cholesky), which matters late in the IPM where kappa(Q) is large.
+// A diagonal pivot of the Schur complement below 1e-14 of the original diagonal entry of Q is
+// reported as a lost pivot (FL_BREAK).
 
-// A pivot counts as lost when it falls below 1e-12 of the original diagonal entry of Q, i.e.
-// when Q is numerically singular (condition number beyond ~1e12).
-__global__ void __launch_bounds__(256) k_gj_pivot(const double* __restrict__ M,
-                                                  const double* __restrict__ Q0, int mp, int kb,
-                                                  double* __restrict__ Pinv, int* fl) {
-  __shared__ double P[kNB][kNB + 1];
-  __shared__ double f[kNB];
-  if (fl[FL_BREAK]) return;
+// Cholesky of a kNB x kNB SPD tile in shared memory (lower triangle, in place), then X = L^{-1}
+// (lower triangular, zeros above).  Needs blockDim.x >= kNB.  Returns false on a lost pivot.
+__device__ bool chol_inv_tile(double (*P)[kNB + 1], double (*Xs)[kNB + 1], const double* q0) {
   const int tid = threadIdx.x;
-  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
-    P[i][j] = M[(size_t)(kb * kNB + i) * mp + kb * kNB + j];
-  }
-  __syncthreads();
-  bool bad = false;
+  bool ok = true;
   for (int p = 0; p < kNB; ++p) {
-    const double piv = P[p][p];
-    const double q0 = Q0[(size_t)(kb * kNB + p) * mp + kb * kNB + p];
-    if (!(piv > 1e-12 * q0) || !isfinite(piv)) bad = true;
-    if (tid < kNB) f[tid] = P[tid][p];
     __syncthreads();
-    const double ip = 1.0 / piv;
-    if (tid < kNB) P[p][tid] = (tid == p ? 1.0 : P[p][tid]) * ip;
+    double d = P[p][p];
+    if (!(d > 1e-14 * q0[p]) || !isfinite(d)) {
+      ok = false;
+      d = fmax(fabs(q0[p]), 1e-300);   // keep the arithmetic finite; the flag aborts the solve
+    }
+    const double l = sqrt(d);
+    __syncthreads();
+    if (tid == 0) P[p][p] = l;
+    if (tid > p && tid < kNB) P[tid][p] /= l;
     __syncthreads();
     for (int e = tid; e < kNB * kNB; e += blockDim.x) {
       const int i = e / kNB, j = e % kNB;
-      if (i != p) P[i][j] = (j == p ? 0.0 : P[i][j]) - f[i] * P[p][j];
+      if (j > p && j <= i) P[i][j] -= P[i][p] * P[j][p];
     }
-    __syncthreads();
   }
-  if (bad && tid == 0) fl[FL_BREAK] = 1;
-  for (int e = tid; e < kNB * kNB; e += blockDim.x) Pinv[e] = P[e / kNB][e % kNB];
+  __syncthreads();
+  if (tid < kNB) {   // column tid of L^{-1} by forward substitution
+    const int j = tid;
+    for (int i = 0; i < kNB; ++i) {
+      if (i < j) {
+        Xs[i][j] = 0.0;
+        continue;
+      }
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int q = j; q < i; ++q) s -= P[i][q] * Xs[q][j];
+      Xs[i][j] = s / P[i][i];
+    }
+  }
+  __syncthreads();
+  return ok;
 }
 
-// T[:, jb] = Pinv * M[kb, jb] (row block of the pivot, 32 x mp); C[jb, :] = M[jb, kb].
-__global__ void __launch_bounds__(256) k_gj_panel(const double* __restrict__ M, int mp, int kb,
-                                                  const double* __restrict__ Pinv,
-                                                  double* __restrict__ T, double* __restrict__ C,
-                                                  const int* fl) {
-  __shared__ double Ps[kNB][kNB + 1];
+__device__ __forceinline__ void tri_decode(int idx, int& i, int& j) {
+  i = 0;
+  while ((i + 1) * (i + 2) / 2 <= idx) ++i;
+  j = idx - i * (i + 1) / 2;
+}
+
+__device__ __forceinline__ void load_tile(double (*S)[kNB + 1], const double* src, int ld) {
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x)
+    S[e / kNB][e % kNB] = src[(size_t)(e / kNB) * ld + e % kNB];
+}
+
+__device__ __forceinline__ void store_tile(double* dst, int ld, double (*S)[kNB + 1]) {
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x)
+    dst[(size_t)(e / kNB) * ld + e % kNB] = S[e / kNB][e % kNB];
+}
+
+__global__ void __launch_bounds__(256) k_ch_diag0(double* __restrict__ M, double* __restrict__ X,
+                                                  const double* __restrict__ Q0, int mp, int* fl) {
+  __shared__ double P[kNB][kNB + 1];
   __shared__ double Xs[kNB][kNB + 1];
+  __shared__ double q0[kNB];
   if (fl[FL_BREAK]) return;
-  const int jb = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
-    Ps[i][j] = Pinv[e];
-    Xs[i][j] = M[(size_t)(kb * kNB + i) * mp + jb * kNB + j];
-    C[(size_t)(jb * kNB + i) * kNB + j] = M[(size_t)(jb * kNB + i) * mp + kb * kNB + j];
-  }
-  __syncthreads();
-  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
-    double acc = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < kNB; ++k) acc = fma(Ps[i][k], Xs[k][j], acc);
-    T[(size_t)i * mp + jb * kNB + j] = acc;
-  }
+  load_tile(P, M, mp);
+  if (threadIdx.x < kNB) q0[threadIdx.x] = Q0[(size_t)threadIdx.x * mp + threadIdx.x];
+  const bool ok = chol_inv_tile(P, Xs, q0);
+  if (!ok && threadIdx.x == 0) fl[FL_BREAK] = 1;
+  store_tile(M, mp, P);
+  store_tile(X, mp, Xs);
 }
 
-__global__ void __launch_bounds__(256) k_gj_update(double* __restrict__ M, int mp, int kb,
-                                                   const double* __restrict__ Pinv,
-                                                   const double* __restrict__ T,
-                                                   const double* __restrict__ C, const int* fl) {
-  __shared__ double Cs[kNB][kNB + 1];
-  __shared__ double Ts[kNB][kNB + 1];
+// grid: (nbk-kb-1) panel CTAs, then kb row-scaling CTAs
+__global__ void __launch_bounds__(256) k_ch_panel(double* __restrict__ M, double* __restrict__ X,
+                                                  int mp, int nbk, int kb, const int* fl) {
+  __shared__ double Ss[kNB][kNB + 1];
+  __shared__ double Xk[kNB][kNB + 1];
   if (fl[FL_BREAK]) return;
-  const int ib = blockIdx.y, jb = blockIdx.x, tid = threadIdx.x;
-  if (ib == kb && jb == kb) {
-    for (int e = tid; e < kNB * kNB; e += blockDim.x)
-      M[(size_t)(kb * kNB + e / kNB) * mp + kb * kNB + e % kNB] = Pinv[e];
-    return;
+  const int npan = nbk - kb - 1;
+  load_tile(Xk, X + (size_t)(kb * kNB) * mp + kb * kNB, mp);
+  double* dst;
+  const bool panel = (int)blockIdx.x < npan;
+  if (panel) {
+    const int i = kb + 1 + blockIdx.x;
+    dst = M + (size_t)(i * kNB) * mp + kb * kNB;          // A_ik -> L_ik
+  } else {
+    const int j = blockIdx.x - npan;
+    dst = X + (size_t)(kb * kNB) * mp + j * kNB;          // X_kj
   }
-  if (ib == kb) {
-    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-      const int i = e / kNB, j = e % kNB;
-      M[(size_t)(kb * kNB + i) * mp + jb * kNB + j] = T[(size_t)i * mp + jb * kNB + j];
-    }
-    return;
-  }
-  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
-    Cs[i][j] = C[(size_t)(ib * kNB + i) * kNB + j];
-    Ts[i][j] = (jb == kb) ? Pinv[e] : T[(size_t)i * mp + jb * kNB + j];
-  }
+  load_tile(Ss, dst, mp);
   __syncthreads();
-  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-    const int i = e / kNB, j = e % kNB;
+  double out[4];
+  int cnt = 0;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
+    const int r = e / kNB, cc = e % kNB;
+    double acc = 0.0;
+    if (panel) {
+#pragma unroll 8
+      for (int q = 0; q < kNB; ++q) acc = fma(Ss[r][q], Xk[cc][q], acc);   // A_ik X_kk^T
+    } else {
+#pragma unroll 8
+      for (int q = 0; q < kNB; ++q) acc = fma(Xk[r][q], Ss[q][cc], acc);   // X_kk X_kj
+    }
+    out[cnt] = acc;
+  }
+  cnt = 0;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt)
+    dst[(size_t)(e / kNB) * mp + e % kNB] = out[cnt];
+}
+
+// grid: r(r+1)/2 trailing Cholesky tiles (next diagonal block first), then r(kb+1) inverse
+// tiles, r = nbk - kb - 1.
+__global__ void __launch_bounds__(256) k_ch_update(double* __restrict__ M, double* __restrict__ X,
+                                                   const double* __restrict__ Q0, int mp, int nbk,
+                                                   int kb, int* fl) {
+  __shared__ double As[kNB][kNB + 1];
+  __shared__ double Bs[kNB][kNB + 1];
+  __shared__ double Xs[kNB][kNB + 1];
+  __shared__ double q0[kNB];
+  if (fl[FL_BREAK]) return;
+  const int r = nbk - kb - 1;
+  const int n1 = r * (r + 1) / 2;
+  int b = blockIdx.x;
+  double* tile;
+  if (b < n1) {
+    int ii, jj;
+    if (b == 0) {
+      ii = jj = 0;
+    } else {
+      tri_decode(b, ii, jj);   // index 0 is (0, 0), the next diagonal block
+    }
+    const int i = kb + 1 + ii, j = kb + 1 + jj;
+    tile = M + (size_t)(i * kNB) * mp + j * kNB;
+    load_tile(As, M + (size_t)(i * kNB) * mp + kb * kNB, mp);   // L_ik
+    load_tile(Bs, M + (size_t)(j * kNB) * mp + kb * kNB, mp);   // L_jk
+    __syncthreads();
+    double upd[4];
+    int cnt = 0;
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
+      const int rr = e / kNB, cc = e % kNB;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int q = 0; q < kNB; ++q) acc = fma(As[rr][q], Bs[cc][q], acc);
+      upd[cnt] = tile[(size_t)rr * mp + cc] - acc;
+    }
+    if (ii == 0 && jj == 0) {
+      __syncthreads();
+      cnt = 0;
+      for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) As[e / kNB][e % kNB] = upd[cnt];
+      if (threadIdx.x < kNB) q0[threadIdx.x] = Q0[(size_t)(i * kNB + threadIdx.x) * mp + i * kNB + threadIdx.x];
+      const bool ok = chol_inv_tile(As, Xs, q0);
+      if (!ok && threadIdx.x == 0) fl[FL_BREAK] = 1;
+      store_tile(tile, mp, As);
+      store_tile(X + (size_t)(i * kNB) * mp + i * kNB, mp, Xs);
+      return;
+    }
+    cnt = 0;
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt)
+      tile[(size_t)(e / kNB) * mp + e % kNB] = upd[cnt];
+    return;
+  }
+  b -= n1;
+  const int i = kb + 1 + b / (kb + 1), j = b % (kb + 1);
+  tile = X + (size_t)(i * kNB) * mp + j * kNB;
+  load_tile(As, M + (size_t)(i * kNB) * mp + kb * kNB, mp);    // L_ik
+  load_tile(Bs, X + (size_t)(kb * kNB) * mp + j * kNB, mp);    // X_kj
+  __syncthreads();
+  double upd[4];
+  int cnt = 0;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
+    const int rr = e / kNB, cc = e % kNB;
     double acc = 0.0;
 #pragma unroll 8
-    for (int k = 0; k < kNB; ++k) acc = fma(Cs[i][k], Ts[k][j], acc);
-    double* dst = &M[(size_t)(ib * kNB + i) * mp + jb * kNB + j];
-    if (jb == kb)
-      *dst = -acc;          // column block of the pivot: -C Pinv
-    else
-      *dst = *dst - acc;    // Schur update
+    for (int q = 0; q < kNB; ++q) acc = fma(As[rr][q], Bs[q][cc], acc);
+    upd[cnt] = tile[(size_t)rr * mp + cc] - acc;
+  }
+  cnt = 0;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt)
+    tile[(size_t)(e / kNB) * mp + e % kNB] = upd[cnt];
+}
+
+// M = X^T X for lower tiles (i >= j), sum over block rows q >= i, mirrored into the upper tiles.
+__global__ void __launch_bounds__(256) k_ch_xtx(const double* __restrict__ X, double* __restrict__ M,
+                                                int mp, int nbk, const int* fl) {
+  __shared__ double Xi[kNB][kNB + 1];
+  __shared__ double Xj[kNB][kNB + 1];
+  if (fl[FL_BREAK]) return;
+  int i, j;
+  tri_decode(blockIdx.x, i, j);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = i; q < nbk; ++q) {
+    __syncthreads();
+    load_tile(Xi, X + (size_t)(q * kNB) * mp + i * kNB, mp);
+    load_tile(Xj, X + (size_t)(q * kNB) * mp + j * kNB, mp);
+    __syncthreads();
+    int cnt = 0;
+    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
+      const int rr = e / kNB, cc = e % kNB;
+      double a = acc[cnt];
+#pragma unroll 8
+      for (int t = 0; t < kNB; ++t) a = fma(Xi[t][rr], Xj[t][cc], a);
+      acc[cnt] = a;
+    }
+  }
+  int cnt = 0;
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
+    const int rr = e / kNB, cc = e % kNB;
+    M[(size_t)(i * kNB + rr) * mp + j * kNB + cc] = acc[cnt];
+    if (i != j) M[(size_t)(j * kNB + cc) * mp + i * kNB + rr] = acc[cnt];
   }
 }
 
@@ -216,14 +337,21 @@ cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_gj_inverse(double* M, const double* Q0, int mp, double* Pinv, double* T,
-                              double* C, int* fl, cudaStream_t st) {
-  const int nb = mp / kNB;
-  for (int kb = 0; kb < nb; ++kb) {
-    { note_launch(); k_gj_pivot<<<1, 256, 0, st>>>(M, Q0, mp, kb, Pinv, fl); }
-    { note_launch(); k_gj_panel<<<nb, 256, 0, st>>>(M, mp, kb, Pinv, T, C, fl); }
-    { note_launch(); k_gj_update<<<dim3(nb, nb), 256, 0, st>>>(M, mp, kb, Pinv, T, C, fl); }
+// M (mp x mp, holding Q on entry) becomes Q^{-1}; X is an mp x mp work buffer (L^{-1}).
+cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int* fl,
+                                cudaStream_t st) {
+  const int nbk = mp / kNB;
+  cudaError_t e = cudaMemsetAsync(X, 0, (size_t)mp * mp * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  { note_launch(); k_ch_diag0<<<1, 256, 0, st>>>(M, X, Q0, mp, fl); }
+  for (int kb = 0; kb < nbk; ++kb) {
+    const int r = nbk - kb - 1;
+    const int npanel = r + kb;
+    if (npanel > 0) { note_launch(); k_ch_panel<<<npanel, 256, 0, st>>>(M, X, mp, nbk, kb, fl); }
+    const int nupd = r * (r + 1) / 2 + r * (kb + 1);
+    if (nupd > 0) { note_launch(); k_ch_update<<<nupd, 256, 0, st>>>(M, X, Q0, mp, nbk, kb, fl); }
   }
+  { note_launch(); k_ch_xtx<<<nbk * (nbk + 1) / 2, 256, 0, st>>>(X, M, mp, nbk, fl); }
   return cudaGetLastError();
 }
 

@@ -266,6 +266,7 @@ __global__ void k_vec_ops(int op, double* a, const double* b, const double* c, i
       case VOP_ADD: a[i] = b[i] + c[i]; break;
       case VOP_SUB: a[i] = b[i] - c[i]; break;
       case VOP_NEG: a[i] = -b[i]; break;
+      case VOP_ONES: a[i] = 1.0; break;
     }
   }
 }

@@ -125,7 +125,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   void* bufs[] = {c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->G,
-                  c->u, c->Q, c->M, c->Pinv, c->T, c->C, c->Qsplit, c->sc, c->fl, c->bpart,
+                  c->u, c->Q, c->M, c->X, c->Pinv, c->T, c->C, c->Qsplit, c->sc, c->fl, c->bpart,
                   c->bcnt};
   for (void* p : bufs) dfree(p);
   if (c->sc_h) cudaFreeHost(c->sc_h);
@@ -169,7 +169,8 @@ static lp_status alloc_workspace(lp_ctx* c) {
   c->mp = round_up(m, 64);
   LP_TRY(dalloc(&c->Q, (size_t)c->mp * c->mp));
   LP_TRY(dalloc(&c->M, (size_t)c->mp * c->mp));
-  LP_TRY(dalloc(&c->Pinv, (size_t)kNB * kNB));
+  LP_TRY(dalloc(&c->X, (size_t)c->mp * c->mp));
+  LP_TRY(dalloc(&c->Pinv, (size_t)2 * kNB * kNB));
   LP_TRY(dalloc(&c->T, (size_t)kNB * c->mp));
   LP_TRY(dalloc(&c->C, (size_t)c->mp * kNB));
   c->qsplit = gram_split(m, c->w, c->num_sms);
@@ -621,9 +622,18 @@ static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
     LP_CU(cudaMemcpyAsync(c->M, c->Q, (size_t)c->mp * c->mp * sizeof(double),
                           cudaMemcpyDeviceToDevice, c->st));
     if (eps > 0.0) LP_CU(launch_shift_diag(c->M, c->mp, c->m, eps, c->st));
-    LP_CU(launch_gj_inverse(c->M, c->Q, c->mp, c->Pinv, c->T, c->C, c->fl, c->st));
+    LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->fl, c->st));
+    // a-posteriori check on a fixed probe v = 1: ||Q (M v) - v|| / ||v|| must be small
+    LP_CU(launch_vec_ops(VOP_ONES, c->res, nullptr, nullptr, c->m, nullptr, c->st));
+    LP_CU(launch_symv_dot(c->M, c->mp, c->m, c->res, c->tm, c->sc, c->fl, c->bpart, c->bcnt,
+                          SYMV_PLAIN, c->st));
+    LP_CU(launch_symv_dot(c->Q, c->mp, c->m, c->tm, c->rhs, c->sc, c->fl, c->bpart, c->bcnt,
+                          SYMV_PLAIN, c->st));
+    LP_CU(launch_vec_ops(VOP_SUB, c->rhs, c->rhs, c->res, c->m, nullptr, c->st));
+    LP_CU(launch_norm2(c->rhs, c->m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
     LP_TRY(sync_scalars(c));
-    if (!c->fl_h[FL_BREAK]) break;
+    const double qerr = sqrt(c->sc_h[SC_RES2] / (double)c->m);
+    if (!c->fl_h[FL_BREAK] && qerr < 0.5) break;
     eps = eps > 0.0 ? eps * 100.0 : 1e-10;
     if (!allow_shift || eps > 1e-4)
       return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (pivot lost in the inverse)");
@@ -677,6 +687,7 @@ struct SolveOut {
   int cg_iters = 0;
   int refine = 0;
   double f_norm = 0.0;
+  double f_target = 0.0;
 };
 
 // Alg. 1 (sketch, factor, PCG with FP64 residual refinement) and the FP64 correction data of
@@ -702,10 +713,12 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
       target2 = std::min(c->prm.cg_rel_tol * c->prm.cg_rel_tol * rho0,
                          isfinite(abs_thr) ? abs_thr * abs_thr : INFINITY);
     } else {
-      // refinement: solve (A D^2 A^T) delta = -r~ and add it to dy
+      // refinement: solve (A D^2 A^T) delta = -r~ and add it to dy.  The residual of
+      // dy + delta is the residual of this solve, so it stops at the solve's own target
+      // (relative rule off: a relative 1e-6 of the already small residual would over-solve).
       LP_CU(launch_vec_ops(VOP_NEG, c->rhs, c->rtil, nullptr, m, nullptr, c->st));
-      LP_TRY(run_pcg(c, 0, c->rhs, c->dy, c->prm.cg_rel_tol, abs_thr, c->prm.cg_max_iter, &it,
-                     &r0, &rl));
+      LP_TRY(run_pcg(c, 0, c->rhs, c->dy, INFINITY, 0.5 * sqrt(target2), c->prm.cg_max_iter,
+                     &it, &r0, &rl));
       LP_CU(launch_vec_ops(VOP_ADD, c->dyacc, c->dyacc, c->dy, m, nullptr, c->st));
     }
     total_it += it;
@@ -721,6 +734,7 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
     const double f2 = c->sc_h[SC_F2];
     if (!isfinite(f2)) return fail(LP_ERR_NUMERIC, "non-finite residual in the normal solve");
     so->f_norm = sqrt(std::max(f2, 0.0));
+    so->f_target = sqrt(target2);
     if (!lowprec || f2 <= 4.0 * target2 || outer >= c->prm.refine_max) break;
     ++outer;
   }
@@ -813,6 +827,7 @@ extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, in
     inf.cg_iters_last = so.cg_iters;
     inf.refine_steps = so.refine;
     inf.f_norm = so.f_norm;
+    inf.f_target = so.f_target;
     st = run_step(c, c->x, c->y, c->s, c->rd, c->dyacc, c->t, nullptr, eta, mu0, c->dx, c->ds);
     if (st != LP_OK) {
       result = st;
@@ -866,6 +881,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
     inf.cg_iters_total = so.cg_iters;
     inf.refine_steps = so.refine;
     inf.f_norm = so.f_norm;
+    inf.f_target = so.f_target;
     inf.mu = mu;
     *info = inf;
   }

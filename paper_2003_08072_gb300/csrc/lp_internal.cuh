@@ -116,6 +116,7 @@ struct lp_ctx {
   int mp = 0;                  // m rounded up to kNB
   double* Q = nullptr;         // mp x mp row-major (full symmetric)
   double* M = nullptr;         // Q^{-1}, mp x mp row-major (full symmetric)
+  double* X = nullptr;         // L^{-1} work buffer of the factor, mp x mp
   double* Pinv = nullptr;      // kNB x kNB
   double* T = nullptr;         // kNB x mp
   double* C = nullptr;         // mp x kNB
@@ -250,8 +251,8 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
 cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* Q, double* Qsplit,
                         int split, cudaStream_t st);
 cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t st);
-cudaError_t launch_gj_inverse(double* M, const double* Q0, int mp, double* Pinv, double* T,
-                              double* C, int* fl, cudaStream_t st);
+cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int* fl,
+                                cudaStream_t st);
 
 // CG / preconditioner
 cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, double* z,
@@ -270,7 +271,7 @@ cudaError_t launch_cg_dir(double* d, const double* z, int m, const double* sc, c
                           cudaStream_t st);
 cudaError_t launch_vec_ops(int op, double* a, const double* b, const double* c, int m,
                            const double* sc, cudaStream_t st);
-enum VecOp { VOP_COPY = 0, VOP_ZERO = 1, VOP_ADD = 2, VOP_SUB = 3, VOP_NEG = 4 };
+enum VecOp { VOP_COPY = 0, VOP_ZERO = 1, VOP_ADD = 2, VOP_SUB = 3, VOP_NEG = 4, VOP_ONES = 5 };
 
 // IPM update
 cudaError_t launch_update_dirs(const double* x, const double* s, const double* d2, const double* d,

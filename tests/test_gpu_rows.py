@@ -272,7 +272,10 @@ def test_normal_solve_low_precision_refined(sd):
     p = iipm.rhs_p(A, lp.b, x, sv, rp, rd, mu, 0.5)
     o64 = s64.normal_solve(T(x), T(sv), T(p), 2)
     olo = slo.normal_solve(T(x), T(sv), T(p), 2)
-    assert olo["info"].f_norm <= 2.0 * max(o64["info"].f_norm, 1e-300) + 1e-12
+    # FP64 CG stops at its target; the refined low-precision solve meets twice the target
+    assert o64["info"].f_norm <= o64["info"].f_target * (1 + 1e-6)
+    assert olo["info"].f_norm <= 2.0 * olo["info"].f_target
+    assert abs(olo["info"].f_target - o64["info"].f_target) <= 1e-9 * o64["info"].f_target
     dy64, dylo = N(o64["dy"]), N(olo["dy"])
     assert np.linalg.norm(dylo - dy64) <= 1e-4 * np.linalg.norm(dy64)
     v = np.sqrt(x * sv) * N(olo["Wu"])
