@@ -169,3 +169,82 @@ __device__ __forceinline__ bool grid_min_last(double& v, double* bpart, unsigned
 }
 
 }  // namespace lpk
+
+namespace lpk {
+
+// ---- double-float arithmetic on FP32 pipes -------------------------------------------------
+// Error-free transformations: TwoSum (Knuth, TAOCP vol. 2) gives s + e = a + b exactly;
+// TwoProduct with a fused multiply-add (as in Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005) gives p + e = a * b exactly.  A value is carried as an
+// unnormalised pair (s, c) whose sum is the result; FP32 numbers times a double coefficient
+// split into two floats give products accurate to ~2^-48 relative.
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// (s, c) += a * (bh + bl).  The leading product is rounded on its own (__fmul_rn is never
+// contracted into an FMA), so that p + pe == a * bh exactly and TwoSum sees the rounded p.
+__device__ __forceinline__ void df_fma(float a, float bh, float bl, float& s, float& c) {
+  const float p = __fmul_rn(a, bh);
+  const float pe = fmaf(a, bh, -p);
+  float t, e;
+  two_sum(s, p, t, e);
+  s = t;
+  c += (e + pe) + a * bl;
+}
+
+// (s1, c1) += (s2, c2), renormalised
+__device__ __forceinline__ void df_add(float& s1, float& c1, float s2, float c2) {
+  float t, e;
+  two_sum(s1, s2, t, e);
+  e += c1 + c2;
+  fast_two_sum(t, e, s1, c1);
+}
+
+// (h, l) = (ah + al) * (bh + bl)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = fmaf(ah, bh, -p);
+  fast_two_sum(p, pe + fmaf(ah, bl, al * bh), h, l);
+}
+
+// Square root and reciprocal of a double-float: the FP32 result refined by one Newton step
+// evaluated with an exact product (Dekker 1971; Hida, Li & Bailey, "Algorithms for quad-double
+// precision floating point arithmetic", 2001).  Inputs positive and normal.
+__device__ __forceinline__ void df_sqrt(float ah, float al, float& h, float& l) {
+  const float x = sqrtf(ah);
+  const float p = __fmul_rn(x, x);
+  const float pe = fmaf(x, x, -p);
+  const float r = (((ah - p) - pe) + al) / (2.f * x);
+  fast_two_sum(x, r, h, l);
+}
+
+__device__ __forceinline__ void df_recip(float bh, float bl, float& h, float& l) {
+  const float y = 1.0f / bh;
+  const float p = __fmul_rn(bh, y);
+  const float pe = fmaf(bh, y, -p);
+  const float e = ((1.0f - p) - pe) - bl * y;   // 1 - (bh + bl) y
+  fast_two_sum(y, y * e, h, l);
+}
+
+__device__ __forceinline__ void df_renorm(float& s, float& c) {
+  float t, e;
+  fast_two_sum(s, c, t, e);
+  s = t;
+  c = e;
+}
+
+}  // namespace lpk

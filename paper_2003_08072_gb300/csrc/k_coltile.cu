@@ -68,9 +68,13 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
     const int64_t mycol = col0 + cl;
     const bool cok = mycol < a.n;
     double pc0 = 0.0, pc1 = 1.0, pc2 = 0.0;
+    float pcf = 0.f;
     if (cok) {
       if constexpr (MODE == MODE_NORMAL) {
-        pc0 = a.d2 ? a.d2[mycol] : 1.0;
+        if (std::is_same<ACC, float>::value && a.d2f)
+          pcf = a.d2f[mycol];
+        else
+          pc0 = a.d2 ? a.d2[mycol] : 1.0;
       } else {
         pc0 = a.x[mycol];
         pc1 = a.s[mycol];
@@ -99,7 +103,10 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
 
     ACC cf[NOUT];
     if constexpr (MODE == MODE_NORMAL) {
-      cf[0] = cok ? (ACC)(pc0 * (double)dot) : (ACC)0;
+      if (std::is_same<ACC, float>::value && a.d2f)
+        cf[0] = cok ? (ACC)(pcf * (float)dot) : (ACC)0;   // FP32 weight: no FP64 work per column
+      else
+        cf[0] = cok ? (ACC)(pc0 * (double)dot) : (ACC)0;
       if (a.colout && warp == 0 && lane < TILE && cok) a.colout[mycol] = (double)dot;
     } else {
       const double rdv = (double)dot + pc1 - pc2;   // (A^T y + s - c)_i
@@ -186,7 +193,15 @@ int launch_t(ColArgs a, int num_sms, cudaStream_t st) {
 // Largest number of CTAs a column-tile pass may use (sizes the partial buffer).
 int coltile_max_grid(int num_sms) { return num_sms * 8; }
 
+int launch_coltile_df(int mode, ColArgs a, int num_sms, cudaStream_t st);   // k_coltile_df.cu
+
 int launch_coltile(lp_dtype ta, bool acc_f64, int mode, ColArgs a, int num_sms, cudaStream_t st) {
+  // FP32 A with FP64-class accumulation runs on the FP32 pipes in double-float arithmetic
+  // (k_coltile_df.cu); the FP64-unit kernel remains for shapes beyond its register budget.
+  if (ta == LP_F32 && acc_f64) {
+    const int g = launch_coltile_df(mode, a, num_sms, st);
+    if (g >= 0) return g;
+  }
   if (mode == MODE_NORMAL) {
     switch (ta) {
       case LP_F64: return launch_t<double, double, MODE_NORMAL>(a, num_sms, st);

@@ -4,8 +4,9 @@
 // iterates dy = Q^{-1/2} z as CG on Eq. precond_alt, so only the operator Q^{-1} is needed.
 // It is formed explicitly so that each CG step applies it as one dense symmetric matrix-vector
 // product over the whole GPU instead of two sequential triangular solves.
-//   1. Gram product G G^T in FP64, lower 64x64 tiles, split along w for parallelism, then
-//      summed and mirrored into a full row-major mp x mp matrix (identity on the padding).
+//   1. Gram product G G^T in double-float arithmetic (FP64-class, on the FP32 pipes), lower
+//      64x64 tiles, split along w for parallelism, then summed in FP64 and mirrored into a full
+//      row-major mp x mp matrix (identity on the padding).
 //   2. Q^{-1} = L^{-T} L^{-1} from a blocked Cholesky factor Q = L L^T (Q is symmetric positive
 //      definite when rank(A D W) = m, Lemma 4.1); a lost pivot flags a numerically singular Q.
 #include "dev_util.cuh"
@@ -15,22 +16,27 @@ namespace lpk {
 constexpr int kGT = 64;   // Gram tile
 constexpr int kGK = 16;   // Gram k-chunk
 
+// One 64 x 64 lower tile of G G^T over a slice of the w columns, in double-float arithmetic on
+// the FP32 pipes: each FP64 entry of G is split into hi + lo floats when staged in shared
+// memory; hi*hi products are accumulated with TwoProduct/TwoSum, the cross terms plainly.
 __global__ void __launch_bounds__(256) k_gram_tile(const double* __restrict__ G, int ldg, int m, int w,
                                                    int chunk, double* __restrict__ Qsplit,
                                                    int ntiles) {
-  __shared__ __align__(16) double As[kGK][kGT + 2];
-  __shared__ __align__(16) double Bs[kGK][kGT + 2];
+  __shared__ __align__(16) float Ah[kGK][kGT + 4];
+  __shared__ __align__(16) float Al[kGK][kGT + 4];
+  __shared__ __align__(16) float Bh[kGK][kGT + 4];
+  __shared__ __align__(16) float Bl[kGK][kGT + 4];
   int tile = blockIdx.x, ib = 0;
   while ((ib + 1) * (ib + 2) / 2 <= tile) ++ib;
   const int jb = tile - ib * (ib + 1) / 2;
   const int ks = blockIdx.y;
   const int k0 = ks * chunk, k1 = min(w, k0 + chunk);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  float s[4][4], c[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) s[i][j] = c[i][j] = 0.f;
   for (int k = k0; k < k1; k += kGK) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -38,29 +44,44 @@ __global__ void __launch_bounds__(256) k_gram_tile(const double* __restrict__ G,
       const int kk = idx >> 6, r = idx & 63;
       const int ra = ib * kGT + r, rb = jb * kGT + r;
       const bool kin = (k + kk) < k1;
-      As[kk][r] = (kin && ra < m) ? G[(size_t)(k + kk) * ldg + ra] : 0.0;
-      Bs[kk][r] = (kin && rb < m) ? G[(size_t)(k + kk) * ldg + rb] : 0.0;
+      split_double((kin && ra < m) ? G[(size_t)(k + kk) * ldg + ra] : 0.0, Ah[kk][r], Al[kk][r]);
+      split_double((kin && rb < m) ? G[(size_t)(k + kk) * ldg + rb] : 0.0, Bh[kk][r], Bl[kk][r]);
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 4
     for (int kk = 0; kk < kGK; ++kk) {
-      double a[4], b[4];
+      float ah[4], al[4], bh[4], bl[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Ah[kk][ty * 4 + i];
+        al[i] = Al[kk][ty * 4 + i];
+        bh[i] = Bh[kk][tx * 4 + i];
+        bl[i] = Bl[kk][tx * 4 + i];
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) {
+          const float p = __fmul_rn(ah[i], bh[j]);
+          const float pe = fmaf(ah[i], bh[j], -p);
+          float t, e;
+          two_sum(s[i][j], p, t, e);
+          s[i][j] = t;
+          c[i][j] += (e + pe) + fmaf(ah[i], bl[j], al[i] * bh[j]);
+        }
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) df_renorm(s[i][j], c[i][j]);
     __syncthreads();
   }
   double* out = Qsplit + ((size_t)ks * ntiles + tile) * (kGT * kGT);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * kGT + tx * 4 + j] = acc[i][j];
+    for (int j = 0; j < 4; ++j)
+      out[(ty * 4 + i) * kGT + tx * 4 + j] = (double)s[i][j] + (double)c[i][j];
 }
 
 __global__ void __launch_bounds__(256) k_gram_finish(const double* __restrict__ Qsplit, int split,
@@ -117,21 +138,29 @@ cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* 
 // reported as a lost pivot (FL_BREAK).
 
 // Cholesky of a kNB x kNB SPD tile in shared memory (lower triangle, in place), then X = L^{-1}
-// (lower triangular, zeros above).  Needs blockDim.x >= kNB.  Returns false on a lost pivot.
+// (lower triangular, zeros above).  Needs blockDim.x == 256.  Returns false on a lost pivot.
+// One thread takes each square root and reciprocal (FP64 division and square root are slow
+// on this GPU); everything else multiplies by the broadcast reciprocal.
 __device__ bool chol_inv_tile(double (*P)[kNB + 1], double (*Xs)[kNB + 1], const double* q0) {
+  __shared__ double s_inv[kNB];
+  __shared__ int s_ok;
   const int tid = threadIdx.x;
-  bool ok = true;
+  if (tid == 0) s_ok = 1;
   for (int p = 0; p < kNB; ++p) {
     __syncthreads();
-    double d = P[p][p];
-    if (!(d > 1e-14 * q0[p]) || !isfinite(d)) {
-      ok = false;
-      d = fmax(fabs(q0[p]), 1e-300);   // keep the arithmetic finite; the flag aborts the solve
+    if (tid == 0) {
+      double d = P[p][p];
+      if (!(d > 1e-14 * q0[p]) || !isfinite(d)) {
+        s_ok = 0;
+        d = fmax(fabs(q0[p]), 1e-300);   // keep the arithmetic finite; the flag aborts the solve
+      }
+      const double l = sqrt(d);
+      P[p][p] = l;
+      s_inv[p] = 1.0 / l;
     }
-    const double l = sqrt(d);
     __syncthreads();
-    if (tid == 0) P[p][p] = l;
-    if (tid > p && tid < kNB) P[tid][p] /= l;
+    const double inv = s_inv[p];
+    if (tid > p && tid < kNB) P[tid][p] *= inv;
     __syncthreads();
     for (int e = tid; e < kNB * kNB; e += blockDim.x) {
       const int i = e / kNB, j = e % kNB;
@@ -139,20 +168,20 @@ __device__ bool chol_inv_tile(double (*P)[kNB + 1], double (*Xs)[kNB + 1], const
     }
   }
   __syncthreads();
-  if (tid < kNB) {   // column tid of L^{-1} by forward substitution
-    const int j = tid;
-    for (int i = 0; i < kNB; ++i) {
-      if (i < j) {
-        Xs[i][j] = 0.0;
-        continue;
-      }
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int q = j; q < i; ++q) s -= P[i][q] * Xs[q][j];
-      Xs[i][j] = s / P[i][i];
-    }
+  // X = L^{-1}, row by row: X_ij = -inv_ii sum_{j<=q<i} L_iq X_qj (j < i), X_ii = inv_ii.
+  // 8 threads per column j share the sum over q and reduce with shuffles.
+  const int j = tid >> 3, part = tid & 7;
+  for (int i = 0; i < kNB; ++i) {
+    double s = 0.0;
+    if (j < i)
+      for (int q = j + part; q < i; q += 8) s = fma(P[i][q], Xs[q][j], s);
+    s += __shfl_xor_sync(kFull, s, 4);
+    s += __shfl_xor_sync(kFull, s, 2);
+    s += __shfl_xor_sync(kFull, s, 1);
+    if (part == 0) Xs[i][j] = (j < i) ? -s * s_inv[i] : (j == i ? s_inv[i] : 0.0);
+    __syncthreads();
   }
-  __syncthreads();
-  return ok;
+  return s_ok != 0;
 }
 
 __device__ __forceinline__ void tri_decode(int idx, int& i, int& j) {
@@ -161,168 +190,338 @@ __device__ __forceinline__ void tri_decode(int idx, int& i, int& j) {
   j = idx - i * (i + 1) / 2;
 }
 
-__device__ __forceinline__ void load_tile(double (*S)[kNB + 1], const double* src, int ld) {
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x)
-    S[e / kNB][e % kNB] = src[(size_t)(e / kNB) * ld + e % kNB];
+// ---- double-float tiles: the factorization keeps A/L, X = L^{-1} and M = Q^{-1} as pairs of
+// float matrices (hi, lo); tile products run on the FP32 pipes (see dev_util.cuh).
+struct DFTile {
+  float h[kNB][kNB + 1];
+  float l[kNB][kNB + 1];
+};
+
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& s, float& c) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = fmaf(ah, bh, -p);
+  float t, e;
+  two_sum(s, p, t, e);
+  s = t;
+  c += (e + pe) + fmaf(ah, bl, al * bh);
 }
 
-__device__ __forceinline__ void store_tile(double* dst, int ld, double (*S)[kNB + 1]) {
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x)
-    dst[(size_t)(e / kNB) * ld + e % kNB] = S[e / kNB][e % kNB];
+__device__ __forceinline__ void load_df(DFTile& T, const float* h, const float* l, size_t off, int ld) {
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const size_t a = off + (size_t)(e / kNB) * ld + e % kNB;
+    T.h[e / kNB][e % kNB] = h[a];
+    T.l[e / kNB][e % kNB] = l[a];
+  }
 }
 
-__global__ void __launch_bounds__(256) k_ch_diag0(double* __restrict__ M, double* __restrict__ X,
+
+// out[k] = sum_q A[r][q] * B(q, c) for the 4 elements e = tid + 256 k (r = e / 32, c = e % 32);
+// TRB: B(q, c) = B[c][q] (A B^T), else B[q][c] (A B).  TRA: A(r, q) = A[q][r] (A^T B).
+template <bool TRA, bool TRB>
+__device__ __forceinline__ void df_tile_mul(const DFTile& A, const DFTile& B, float (&s)[4],
+                                            float (&c)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + 256 * k, r = e / kNB, cc = e % kNB;
+    float ss = 0.f, c2 = 0.f;
+#pragma unroll 8
+    for (int q = 0; q < kNB; ++q) {
+      const float ah = TRA ? A.h[q][r] : A.h[r][q];
+      const float al = TRA ? A.l[q][r] : A.l[r][q];
+      const float bh = TRB ? B.h[cc][q] : B.h[q][cc];
+      const float bl = TRB ? B.l[cc][q] : B.l[q][cc];
+      df_mac(ah, al, bh, bl, ss, c2);
+    }
+    s[k] = ss;
+    c[k] = c2;
+  }
+}
+
+// Factor and invert a diagonal block in double-float arithmetic: T (DF tile, SPD) is replaced
+// by its Cholesky factor L (lower triangle) in place, X receives L^{-1}; both are written to
+// global DF storage at offset off.  One thread takes each square root and reciprocal; the
+// trailing updates and the triangular inverse use all 256 threads.  A Schur pivot below 1e-14
+// of the original diagonal entry of Q (q0) counts as lost: returns false.
+__device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl, size_t off, int mp,
+                           const double* q0, DFTile& X) {
+  __shared__ float inv_h[kNB], inv_l[kNB];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_ok = 1;
+  for (int p = 0; p < kNB; ++p) {
+    __syncthreads();
+    if (tid == 0) {
+      float dh = T.h[p][p], dl = T.l[p][p];
+      if (!((double)dh + (double)dl > 1e-14 * q0[p]) || !isfinite(dh)) {
+        s_ok = 0;
+        dh = (float)fmax(fabs(q0[p]), 1e-30);   // keep the arithmetic finite; the flag aborts
+        dl = 0.f;
+      }
+      float lh, ll, ih, il;
+      df_sqrt(dh, dl, lh, ll);
+      df_recip(lh, ll, ih, il);
+      T.h[p][p] = lh;
+      T.l[p][p] = ll;
+      inv_h[p] = ih;
+      inv_l[p] = il;
+    }
+    __syncthreads();
+    if (tid > p && tid < kNB) {
+      float h, l;
+      df_mul(T.h[tid][p], T.l[tid][p], inv_h[p], inv_l[p], h, l);
+      T.h[tid][p] = h;
+      T.l[tid][p] = l;
+    }
+    __syncthreads();
+    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+      const int i = e / kNB, j = e % kNB;
+      if (j > p && j <= i) {
+        float h, l;
+        df_mul(T.h[i][p], T.l[i][p], T.h[j][p], T.l[j][p], h, l);
+        float a = T.h[i][j], b = T.l[i][j];
+        df_add(a, b, -h, -l);
+        T.h[i][j] = a;
+        T.l[i][j] = b;
+      }
+    }
+  }
+  __syncthreads();
+  // X = L^{-1}, row by row: X_ij = -inv_ii sum_{j<=q<i} L_iq X_qj (j < i), X_ii = inv_ii;
+  // 8 threads per column share the sum and reduce with shuffles.
+  const int j = tid >> 3, part = tid & 7;
+  for (int i = 0; i < kNB; ++i) {
+    float s = 0.f, c = 0.f;
+    if (j < i)
+      for (int q = j + part; q < i; q += 8) df_mac(T.h[i][q], T.l[i][q], X.h[q][j], X.l[q][j], s, c);
+#pragma unroll
+    for (int off2 = 4; off2 >= 1; off2 >>= 1)
+      df_add(s, c, __shfl_xor_sync(kFull, s, off2), __shfl_xor_sync(kFull, c, off2));
+    if (part == 0) {
+      float h = 0.f, l = 0.f;
+      if (j < i) {
+        df_mul(s, c, inv_h[i], inv_l[i], h, l);
+        h = -h;
+        l = -l;
+      } else if (j == i) {
+        h = inv_h[i];
+        l = inv_l[i];
+      }
+      X.h[i][j] = h;
+      X.l[i][j] = l;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, cc = e % kNB;
+    const size_t a = off + (size_t)r * mp + cc;
+    Lh[a] = cc <= r ? T.h[r][cc] : 0.f;
+    Ll[a] = cc <= r ? T.l[r][cc] : 0.f;
+    Xh[a] = X.h[r][cc];
+    Xl[a] = X.l[r][cc];
+  }
+  return s_ok != 0;
+}
+
+// Q (FP64, full) -> DF pairs of (Q + eps diag(Q)) in the A/L storage.
+__global__ void k_q_to_df(const double* __restrict__ Q, int mp, int m, double eps,
+                          float* __restrict__ Ah, float* __restrict__ Al) {
+  const size_t total = (size_t)mp * mp;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double v = Q[i];
+    const size_t r = i / mp, cc = i % mp;
+    if (r == cc && (int)r < m) v *= (1.0 + eps);
+    split_double(v, Ah[i], Al[i]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ch_diag0(float* Ah, float* Al, float* Xh, float* Xl,
                                                   const double* __restrict__ Q0, int mp, int* fl) {
-  __shared__ double P[kNB][kNB + 1];
-  __shared__ double Xs[kNB][kNB + 1];
+  __shared__ DFTile T;
+  __shared__ DFTile XT;
   __shared__ double q0[kNB];
   if (fl[FL_BREAK]) return;
-  load_tile(P, M, mp);
+  load_df(T, Ah, Al, 0, mp);
   if (threadIdx.x < kNB) q0[threadIdx.x] = Q0[(size_t)threadIdx.x * mp + threadIdx.x];
-  const bool ok = chol_inv_tile(P, Xs, q0);
+  __syncthreads();
+  const bool ok = diag_block(T, Ah, Al, Xh, Xl, 0, mp, q0, XT);
   if (!ok && threadIdx.x == 0) fl[FL_BREAK] = 1;
-  store_tile(M, mp, P);
-  store_tile(X, mp, Xs);
 }
 
-// grid: (nbk-kb-1) panel CTAs, then kb row-scaling CTAs
-__global__ void __launch_bounds__(256) k_ch_panel(double* __restrict__ M, double* __restrict__ X,
-                                                  int mp, int nbk, int kb, const int* fl) {
-  __shared__ double Ss[kNB][kNB + 1];
-  __shared__ double Xk[kNB][kNB + 1];
+// grid: (nbk-kb-1) panel CTAs L_ik = A_ik X_kk^T, then kb row-scaling CTAs X_kj <- X_kk X_kj.
+__global__ void __launch_bounds__(256) k_ch_panel(float* Ah, float* Al, float* Xh, float* Xl, int mp,
+                                                  int nbk, int kb, const int* fl) {
+  __shared__ DFTile S;
+  __shared__ DFTile XK;
   if (fl[FL_BREAK]) return;
   const int npan = nbk - kb - 1;
-  load_tile(Xk, X + (size_t)(kb * kNB) * mp + kb * kNB, mp);
-  double* dst;
+  load_df(XK, Xh, Xl, (size_t)(kb * kNB) * mp + kb * kNB, mp);
   const bool panel = (int)blockIdx.x < npan;
+  float* dh;
+  float* dl;
+  size_t off;
   if (panel) {
-    const int i = kb + 1 + blockIdx.x;
-    dst = M + (size_t)(i * kNB) * mp + kb * kNB;          // A_ik -> L_ik
+    off = (size_t)((kb + 1 + blockIdx.x) * kNB) * mp + kb * kNB;
+    dh = Ah;
+    dl = Al;
   } else {
-    const int j = blockIdx.x - npan;
-    dst = X + (size_t)(kb * kNB) * mp + j * kNB;          // X_kj
+    off = (size_t)(kb * kNB) * mp + (blockIdx.x - npan) * kNB;
+    dh = Xh;
+    dl = Xl;
   }
-  load_tile(Ss, dst, mp);
+  load_df(S, dh, dl, off, mp);
   __syncthreads();
-  double out[4];
-  int cnt = 0;
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
-    const int r = e / kNB, cc = e % kNB;
-    double acc = 0.0;
-    if (panel) {
-#pragma unroll 8
-      for (int q = 0; q < kNB; ++q) acc = fma(Ss[r][q], Xk[cc][q], acc);   // A_ik X_kk^T
-    } else {
-#pragma unroll 8
-      for (int q = 0; q < kNB; ++q) acc = fma(Xk[r][q], Ss[q][cc], acc);   // X_kk X_kj
-    }
-    out[cnt] = acc;
+  float s[4], c[4];
+  if (panel)
+    df_tile_mul<false, true>(S, XK, s, c);    // A_ik X_kk^T
+  else
+    df_tile_mul<false, false>(XK, S, s, c);   // X_kk X_kj
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const size_t a = off + (size_t)(e / kNB) * mp + e % kNB;
+    float h, l;
+    fast_two_sum(s[k], c[k], h, l);
+    dh[a] = h;
+    dl[a] = l;
   }
-  cnt = 0;
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt)
-    dst[(size_t)(e / kNB) * mp + e % kNB] = out[cnt];
 }
 
-// grid: r(r+1)/2 trailing Cholesky tiles (next diagonal block first), then r(kb+1) inverse
-// tiles, r = nbk - kb - 1.
-__global__ void __launch_bounds__(256) k_ch_update(double* __restrict__ M, double* __restrict__ X,
+// grid: r(r+1)/2 trailing Cholesky tiles (next diagonal block first), then r(kb+1) inverse tiles.
+__global__ void __launch_bounds__(256) k_ch_update(float* Ah, float* Al, float* Xh, float* Xl,
                                                    const double* __restrict__ Q0, int mp, int nbk,
                                                    int kb, int* fl) {
-  __shared__ double As[kNB][kNB + 1];
-  __shared__ double Bs[kNB][kNB + 1];
-  __shared__ double Xs[kNB][kNB + 1];
+  __shared__ DFTile S1;
+  __shared__ DFTile S2;
   __shared__ double q0[kNB];
   if (fl[FL_BREAK]) return;
   const int r = nbk - kb - 1;
   const int n1 = r * (r + 1) / 2;
   int b = blockIdx.x;
-  double* tile;
+  float* dh;
+  float* dl;
+  size_t off;
+  float s[4], c[4];
+  bool diag = false;
+  int i;
   if (b < n1) {
     int ii, jj;
-    if (b == 0) {
-      ii = jj = 0;
-    } else {
-      tri_decode(b, ii, jj);   // index 0 is (0, 0), the next diagonal block
-    }
-    const int i = kb + 1 + ii, j = kb + 1 + jj;
-    tile = M + (size_t)(i * kNB) * mp + j * kNB;
-    load_tile(As, M + (size_t)(i * kNB) * mp + kb * kNB, mp);   // L_ik
-    load_tile(Bs, M + (size_t)(j * kNB) * mp + kb * kNB, mp);   // L_jk
+    tri_decode(b, ii, jj);   // index 0 is (0, 0): the next diagonal block first
+    i = kb + 1 + ii;
+    const int j = kb + 1 + jj;
+    diag = (ii == 0 && jj == 0);
+    off = (size_t)(i * kNB) * mp + j * kNB;
+    dh = Ah;
+    dl = Al;
+    load_df(S1, Ah, Al, (size_t)(i * kNB) * mp + kb * kNB, mp);   // L_ik
+    load_df(S2, Ah, Al, (size_t)(j * kNB) * mp + kb * kNB, mp);   // L_jk
     __syncthreads();
-    double upd[4];
-    int cnt = 0;
-    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
-      const int rr = e / kNB, cc = e % kNB;
-      double acc = 0.0;
-#pragma unroll 8
-      for (int q = 0; q < kNB; ++q) acc = fma(As[rr][q], Bs[cc][q], acc);
-      upd[cnt] = tile[(size_t)rr * mp + cc] - acc;
+    df_tile_mul<false, true>(S1, S2, s, c);                      // L_ik L_jk^T
+  } else {
+    b -= n1;
+    i = kb + 1 + b / (kb + 1);
+    const int j = b % (kb + 1);
+    off = (size_t)(i * kNB) * mp + j * kNB;
+    dh = Xh;
+    dl = Xl;
+    load_df(S1, Ah, Al, (size_t)(i * kNB) * mp + kb * kNB, mp);   // L_ik
+    load_df(S2, Xh, Xl, (size_t)(kb * kNB) * mp + j * kNB, mp);   // X_kj
+    __syncthreads();
+    df_tile_mul<false, false>(S1, S2, s, c);                     // L_ik X_kj
+  }
+  // tile <- tile - (s + c)
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const size_t a = off + (size_t)(e / kNB) * mp + e % kNB;
+    float h = dh[a], l = dl[a];
+    df_add(h, l, -s[k], -c[k]);
+    s[k] = h;
+    c[k] = l;
+  }
+  if (!diag) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      const size_t a = off + (size_t)(e / kNB) * mp + e % kNB;
+      dh[a] = s[k];
+      dl[a] = c[k];
     }
-    if (ii == 0 && jj == 0) {
-      __syncthreads();
-      cnt = 0;
-      for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) As[e / kNB][e % kNB] = upd[cnt];
-      if (threadIdx.x < kNB) q0[threadIdx.x] = Q0[(size_t)(i * kNB + threadIdx.x) * mp + i * kNB + threadIdx.x];
-      const bool ok = chol_inv_tile(As, Xs, q0);
-      if (!ok && threadIdx.x == 0) fl[FL_BREAK] = 1;
-      store_tile(tile, mp, As);
-      store_tile(X + (size_t)(i * kNB) * mp + i * kNB, mp, Xs);
-      return;
-    }
-    cnt = 0;
-    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt)
-      tile[(size_t)(e / kNB) * mp + e % kNB] = upd[cnt];
     return;
   }
-  b -= n1;
-  const int i = kb + 1 + b / (kb + 1), j = b % (kb + 1);
-  tile = X + (size_t)(i * kNB) * mp + j * kNB;
-  load_tile(As, M + (size_t)(i * kNB) * mp + kb * kNB, mp);    // L_ik
-  load_tile(Bs, X + (size_t)(kb * kNB) * mp + j * kNB, mp);    // X_kj
   __syncthreads();
-  double upd[4];
-  int cnt = 0;
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
-    const int rr = e / kNB, cc = e % kNB;
-    double acc = 0.0;
-#pragma unroll 8
-    for (int q = 0; q < kNB; ++q) acc = fma(As[rr][q], Bs[q][cc], acc);
-    upd[cnt] = tile[(size_t)rr * mp + cc] - acc;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    S1.h[e / kNB][e % kNB] = s[k];
+    S1.l[e / kNB][e % kNB] = c[k];
   }
-  cnt = 0;
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt)
-    tile[(size_t)(e / kNB) * mp + e % kNB] = upd[cnt];
+  if (threadIdx.x < kNB) q0[threadIdx.x] = Q0[(size_t)(i * kNB + threadIdx.x) * mp + i * kNB + threadIdx.x];
+  __syncthreads();
+  const bool ok = diag_block(S1, Ah, Al, Xh, Xl, off, mp, q0, S2);
+  if (!ok && threadIdx.x == 0) fl[FL_BREAK] = 1;
 }
 
-// M = X^T X for lower tiles (i >= j), sum over block rows q >= i, mirrored into the upper tiles.
-__global__ void __launch_bounds__(256) k_ch_xtx(const double* __restrict__ X, double* __restrict__ M,
-                                                int mp, int nbk, const int* fl) {
-  __shared__ double Xi[kNB][kNB + 1];
-  __shared__ double Xj[kNB][kNB + 1];
+// M = X^T X (lower tiles, summed over block rows q >= i) stored as DF pairs (Mh, Ml), mirrored.
+__global__ void __launch_bounds__(256) k_ch_xtx(const float* Xh, const float* Xl, float* Mh,
+                                                float* Ml, int mp, int nbk, const int* fl) {
+  __shared__ DFTile Xi;
+  __shared__ DFTile Xj;
   if (fl[FL_BREAK]) return;
   int i, j;
   tri_decode(blockIdx.x, i, j);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
   for (int q = i; q < nbk; ++q) {
     __syncthreads();
-    load_tile(Xi, X + (size_t)(q * kNB) * mp + i * kNB, mp);
-    load_tile(Xj, X + (size_t)(q * kNB) * mp + j * kNB, mp);
+    load_df(Xi, Xh, Xl, (size_t)(q * kNB) * mp + i * kNB, mp);
+    load_df(Xj, Xh, Xl, (size_t)(q * kNB) * mp + j * kNB, mp);
     __syncthreads();
-    int cnt = 0;
-    for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
-      const int rr = e / kNB, cc = e % kNB;
-      double a = acc[cnt];
-#pragma unroll 8
-      for (int t = 0; t < kNB; ++t) a = fma(Xi[t][rr], Xj[t][cc], a);
-      acc[cnt] = a;
+    float s2[4], c2[4];
+    df_tile_mul<true, false>(Xi, Xj, s2, c2);   // X_qi^T X_qj
+#pragma unroll
+    for (int k = 0; k < 4; ++k) df_add(s[k], c[k], s2[k], c2[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = threadIdx.x + 256 * k, rr = e / kNB, cc = e % kNB;
+    const size_t a = (size_t)(i * kNB + rr) * mp + j * kNB + cc;
+    const size_t bsym = (size_t)(j * kNB + cc) * mp + i * kNB + rr;
+    Mh[a] = s[k];
+    Ml[a] = c[k];
+    if (i != j) {
+      Mh[bsym] = s[k];
+      Ml[bsym] = c[k];
     }
   }
-  int cnt = 0;
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x, ++cnt) {
-    const int rr = e / kNB, cc = e % kNB;
-    M[(size_t)(i * kNB + rr) * mp + j * kNB + cc] = acc[cnt];
-    if (i != j) M[(size_t)(j * kNB + cc) * mp + i * kNB + rr] = acc[cnt];
+}
+
+// (Mh + Ml) -> double, m x m with leading dimension ld (for lp_factor's output).
+__global__ void k_df_to_double(const float* Mh, const float* Ml, int mp, int m, double* out, int ld) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)m * m;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / m, cc = i % m;
+    out[r * ld + cc] = (double)Mh[r * mp + cc] + (double)Ml[r * mp + cc];
   }
+}
+
+cudaError_t launch_df_to_double(const double* Mdf, int mp, int m, double* out, int ld,
+                                cudaStream_t st) {
+  const float* Mh = reinterpret_cast<const float*>(Mdf);
+  { note_launch(); k_df_to_double<<<1024, 256, 0, st>>>(Mh, Mh + (size_t)mp * mp, mp, m, out, ld); }
+  return cudaGetLastError();
+}
+
+// out_i += eps Q_ii v_i: turns Q v into (Q + eps diag Q) v for the factor's quality check.
+__global__ void k_add_shift(double* out, const double* Q, int mp, int m, double eps, const double* v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    out[i] += eps * Q[(size_t)i * mp + i] * v[i];
+}
+
+cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double eps,
+                             const double* v, cudaStream_t st) {
+  { note_launch(); k_add_shift<<<(m + 255) / 256, 256, 0, st>>>(out, Q, mp, m, eps, v); }
+  return cudaGetLastError();
 }
 
 // Relative diagonal shift M_ii *= (1 + eps): keeps the preconditioner positive definite when
@@ -337,21 +536,28 @@ cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t
   return cudaGetLastError();
 }
 
-// M (mp x mp, holding Q on entry) becomes Q^{-1}; X is an mp x mp work buffer (L^{-1}).
-cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int* fl,
-                                cudaStream_t st) {
+// Q (FP64, mp x mp) -> M = (Q + eps diag Q)^{-1} as DF pairs in M's storage (Mh = (float*)M,
+// Ml = Mh + mp^2); X (same size) is work space for L^{-1}.
+cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
+                                int* fl, cudaStream_t st) {
   const int nbk = mp / kNB;
-  cudaError_t e = cudaMemsetAsync(X, 0, (size_t)mp * mp * sizeof(double), st);
+  const size_t mm = (size_t)mp * mp;
+  float* Ah = reinterpret_cast<float*>(M);
+  float* Al = Ah + mm;
+  float* Xh = reinterpret_cast<float*>(X);
+  float* Xl = Xh + mm;
+  cudaError_t e = cudaMemsetAsync(X, 0, mm * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  { note_launch(); k_ch_diag0<<<1, 256, 0, st>>>(M, X, Q0, mp, fl); }
+  { note_launch(); k_q_to_df<<<1024, 256, 0, st>>>(Q0, mp, m, eps, Ah, Al); }
+  { note_launch(); k_ch_diag0<<<1, 256, 0, st>>>(Ah, Al, Xh, Xl, Q0, mp, fl); }
   for (int kb = 0; kb < nbk; ++kb) {
     const int r = nbk - kb - 1;
     const int npanel = r + kb;
-    if (npanel > 0) { note_launch(); k_ch_panel<<<npanel, 256, 0, st>>>(M, X, mp, nbk, kb, fl); }
+    if (npanel > 0) { note_launch(); k_ch_panel<<<npanel, 256, 0, st>>>(Ah, Al, Xh, Xl, mp, nbk, kb, fl); }
     const int nupd = r * (r + 1) / 2 + r * (kb + 1);
-    if (nupd > 0) { note_launch(); k_ch_update<<<nupd, 256, 0, st>>>(M, X, Q0, mp, nbk, kb, fl); }
+    if (nupd > 0) { note_launch(); k_ch_update<<<nupd, 256, 0, st>>>(Ah, Al, Xh, Xl, Q0, mp, nbk, kb, fl); }
   }
-  { note_launch(); k_ch_xtx<<<nbk * (nbk + 1) / 2, 256, 0, st>>>(X, M, mp, nbk, fl); }
+  { note_launch(); k_ch_xtx<<<nbk * (nbk + 1) / 2, 256, 0, st>>>(Xh, Xl, Ah, Al, mp, nbk, fl); }
   return cudaGetLastError();
 }
 

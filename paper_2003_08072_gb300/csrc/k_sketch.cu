@@ -83,25 +83,36 @@ cudaError_t launch_sketch_scan(const int32_t* cnt, int w, int32_t* start, int32_
   return cudaGetLastError();
 }
 
+// Bucket scatter of the nonzeros of W.  With d given, each entry also gets its coefficient
+// sign * d_i / sqrt(s) as a double-float pair (computed once per nonzero, not per gather thread).
 __global__ void k_scatter(const int32_t* hb, int64_t n, int s, const int32_t* start,
-                          int32_t* cursor, int32_t* list) {
+                          int32_t* cursor, int32_t* list, const double* d, float2* coef) {
   const int64_t total = n * (int64_t)s;
+  const double inv_sqrt_s = 1.0 / sqrt((double)s);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int32_t h = hb[idx];
     const int32_t b = h & 0x7fffffff;
     const int32_t pos = start[b] + atomicAdd(&cursor[b], 1);
-    list[pos] = (int32_t)(idx / s) | (h & (int32_t)0x80000000);
+    const int64_t col = idx / s;
+    list[pos] = (int32_t)col | (h & (int32_t)0x80000000);
+    if (coef) {
+      const double v = (h < 0 ? -d[col] : d[col]) * inv_sqrt_s;
+      float ch, cl;
+      split_double(v, ch, cl);
+      coef[pos] = make_float2(ch, cl);
+    }
   }
 }
 
 cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, const int32_t* start,
-                                  int32_t* cursor, int32_t* list, cudaStream_t st) {
+                                  int32_t* cursor, int32_t* list, const double* d, float2* coef,
+                                  cudaStream_t st) {
   const int64_t total = n * (int64_t)s;
   int64_t grid = (total + 255) / 256;
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
-  { note_launch(); k_scatter<<<(unsigned)grid, 256, 0, st>>>(hb, n, s, start, cursor, list); }
+  { note_launch(); k_scatter<<<(unsigned)grid, 256, 0, st>>>(hb, n, s, start, cursor, list, d, coef); }
   return cudaGetLastError();
 }
 
@@ -168,6 +179,68 @@ __global__ void __launch_bounds__(512) k_gather_dense(const TA* __restrict__ A, 
     }
 }
 
+// FP32 A: the same gather with double-float accumulation on the FP32 pipes.
+template <int SPW>
+__global__ void __launch_bounds__(512) k_gather_dense_df(const float* __restrict__ A, int64_t lda,
+                                                         int m, const int32_t* __restrict__ start,
+                                                         const int32_t* __restrict__ list,
+                                                         const float2* __restrict__ coef,
+                                                         double* __restrict__ G, int ldg) {
+  constexpr int VEC = 4;
+  constexpr int UNR = 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = blockIdx.x;
+  float as[SPW][VEC], ac[SPW][VEC];
+  int rowb[SPW];
+  bool rok[SPW];
+#pragma unroll
+  for (int sl = 0; sl < SPW; ++sl) {
+    rowb[sl] = ((warp * SPW + sl) * 32 + lane) * VEC;
+    rok[sl] = rowb[sl] < m;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) as[sl][e] = ac[sl][e] = 0.f;
+  }
+  const int e0 = start[b], e1 = start[b + 1];
+  for (int e = e0; e < e1; e += UNR) {
+    uint4 ar[UNR][SPW];
+    float2 cf[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (e + u < e1) {
+        const int64_t col = list[e + u] & 0x7fffffff;
+        cf[u] = coef[e + u];
+#pragma unroll
+        for (int sl = 0; sl < SPW; ++sl)
+          ar[u][sl] = rok[sl] ? ld_stream(A + col * lda + rowb[sl]) : make_uint4(0u, 0u, 0u, 0u);
+      } else {
+        cf[u] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int sl = 0; sl < SPW; ++sl) ar[u][sl] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+#pragma unroll
+      for (int sl = 0; sl < SPW; ++sl) {
+        float av[VEC];
+        unpack<float, float>(ar[u][sl], av);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) df_fma(av[q], cf[u].x, cf[u].y, as[sl][q], ac[sl][q]);
+      }
+#pragma unroll
+    for (int sl = 0; sl < SPW; ++sl)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) df_renorm(as[sl][q], ac[sl][q]);
+  }
+#pragma unroll
+  for (int sl = 0; sl < SPW; ++sl)
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      const int row = rowb[sl] + q;
+      if (rok[sl] && row < m) G[(size_t)b * ldg + row] = (double)as[sl][q] + (double)ac[sl][q];
+    }
+}
+
 template <typename TA>
 static cudaError_t gather_dense_t(const void* A, int64_t lda, int m, int s, int w,
                                   const int32_t* start, const int32_t* list, const double* d,
@@ -189,8 +262,24 @@ static cudaError_t gather_dense_t(const void* A, int64_t lda, int m, int s, int 
 
 cudaError_t launch_sketch_gather_dense(lp_dtype ta, const void* A, int64_t lda, int m, int s,
                                        int w, const int32_t* start, const int32_t* list,
-                                       const double* d, double* G, int ldg, cudaStream_t st) {
+                                       const double* d, double* G, int ldg, cudaStream_t st,
+                                       const float2* coef) {
   if (ta == LP_F64) return gather_dense_t<double>(A, lda, m, s, w, start, list, d, G, ldg, st);
+  if (ta == LP_F32 && coef) {
+    const int nslices = (m + 127) / 128;
+    int spw = 1;
+    while ((nslices + spw - 1) / spw > 16) spw *= 2;
+    const int threads = ((nslices + spw - 1) / spw) * 32;
+    const float* Af = reinterpret_cast<const float*>(A);
+    if (spw == 1) {
+      { note_launch(); k_gather_dense_df<1><<<w, threads, 0, st>>>(Af, lda, m, start, list, coef, G, ldg); }
+      return cudaGetLastError();
+    }
+    if (spw == 2) {
+      { note_launch(); k_gather_dense_df<2><<<w, threads, 0, st>>>(Af, lda, m, start, list, coef, G, ldg); }
+      return cudaGetLastError();
+    }
+  }
   if (ta == LP_F32) return gather_dense_t<float>(A, lda, m, s, w, start, list, d, G, ldg, st);
   return cudaErrorInvalidValue;
 }

@@ -10,15 +10,16 @@ namespace lpk {
 // Partials [nblk][nout][m] -> m-vectors.  32 rows x 8 block groups per CTA.
 // ------------------------------------------------------------------------------------
 template <typename ACC>
-__global__ void __launch_bounds__(256) k_reduce(RedArgs a) {
+__global__ void __launch_bounds__(1024) k_reduce(RedArgs a) {
   if (a.skip_if_done && a.fl[FL_DONE]) return;
-  __shared__ double sh[2][8][33];
+  // 32 rows x 32 block groups per CTA: each thread sums every 32nd partial of one row
+  __shared__ double sh[2][32][33];
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int row = blockIdx.x * 32 + rl;
   const ACC* part = reinterpret_cast<const ACC*>(a.part);
   double s0 = 0.0, s1 = 0.0;
   if (row < a.m) {
-    for (int b = g; b < a.nblk; b += 8) {
+    for (int b = g; b < a.nblk; b += 32) {
       s0 += (double)part[((size_t)b * a.nout) * a.m + row];
       if (a.nout > 1) s1 += (double)part[((size_t)b * a.nout + 1) * a.m + row];
     }
@@ -29,8 +30,8 @@ __global__ void __launch_bounds__(256) k_reduce(RedArgs a) {
   double contrib[2] = {0.0, 0.0};
   if (g == 0) {
     double t0 = 0.0, t1 = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
       t0 += sh[0][k][rl];
       t1 += sh[1][k][rl];
     }
@@ -76,9 +77,9 @@ __global__ void __launch_bounds__(256) k_reduce(RedArgs a) {
 cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st) {
   const int grid = (a.m + 31) / 32;
   if (a.acc_f64)
-    { note_launch(); k_reduce<double><<<grid, 256, 0, st>>>(a); }
+    { note_launch(); k_reduce<double><<<grid, 1024, 0, st>>>(a); }
   else
-    { note_launch(); k_reduce<float><<<grid, 256, 0, st>>>(a); }
+    { note_launch(); k_reduce<float><<<grid, 1024, 0, st>>>(a); }
   return cudaGetLastError();
 }
 
@@ -87,7 +88,8 @@ cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st) {
 // ------------------------------------------------------------------------------------
 __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ s, int64_t n,
                        double* __restrict__ d2, double* __restrict__ d, double* sc, double* bpart,
-                       unsigned* bcnt, double sigma, const double* __restrict__ c) {
+                       unsigned* bcnt, double sigma, const double* __restrict__ c,
+                       float* __restrict__ d2f) {
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -95,6 +97,7 @@ __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ 
     const double q = xi / si;
     d2[i] = q;
     d[i] = sqrt(q);
+    if (d2f) d2f[i] = (float)q;
     v[0] += xi * si;
     v[1] += c[i] * xi;
   }
@@ -115,8 +118,8 @@ static int vec_grid(int64_t n) {
 
 cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
                                 double* sc, double* bpart, unsigned* bcnt, double sigma,
-                                const double* c, cudaStream_t st) {
-  { note_launch(); k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c); }
+                                const double* c, cudaStream_t st, float* d2f) {
+  { note_launch(); k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c, d2f); }
   return cudaGetLastError();
 }
 
@@ -152,19 +155,48 @@ struct SymvArgs {
   double rel2;     // CG relative tolerance squared (CG_INIT)
 };
 
+// DF: M holds double-float pairs (Mh = (float*)M, Ml = Mh + mp^2) and the row sums run on the
+// FP32 pipes; otherwise M is FP64.
+template <bool DF>
 __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
   if (a.mode == SYMV_CG_STEP && a.fl[FL_DONE]) return;
   extern __shared__ double rs[];
-  for (int i = threadIdx.x; i < a.m; i += blockDim.x) rs[i] = a.r[i];
+  float* rh = reinterpret_cast<float*>(rs + a.m);   // DF: r split into hi / lo floats
+  float* rl = rh + a.m;
+  for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
+    const double v = a.r[i];
+    rs[i] = v;
+    if (DF) split_double(v, rh[i], rl[i]);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int row = blockIdx.x * 8 + warp;
   double dotc = 0.0;
   if (row < a.m) {
-    const double* Mr = a.M + (size_t)row * a.mp;
-    double acc = 0.0;
-    for (int j = lane; j < a.m; j += 32) acc = fma(Mr[j], rs[j], acc);
-    acc = warp_sum(acc);
+    double acc;
+    if constexpr (DF) {
+      const float* Mh = reinterpret_cast<const float*>(a.M) + (size_t)row * a.mp;
+      const float* Ml = Mh + (size_t)a.mp * a.mp;
+      float s = 0.f, c = 0.f;
+      for (int j = lane; j < a.m; j += 32) {
+        const float mh = Mh[j], ml = Ml[j];
+        const float p = __fmul_rn(mh, rh[j]);
+        const float pe = fmaf(mh, rh[j], -p);
+        float t, e;
+        two_sum(s, p, t, e);
+        s = t;
+        c += (e + pe) + fmaf(mh, rl[j], ml * rh[j]);
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1)
+        df_add(s, c, __shfl_xor_sync(kFull, s, off), __shfl_xor_sync(kFull, c, off));
+      acc = (double)s + (double)c;
+    } else {
+      const double* Mr = a.M + (size_t)row * a.mp;
+      acc = 0.0;
+      for (int j = lane; j < a.m; j += 32) acc = fma(Mr[j], rs[j], acc);
+      acc = warp_sum(acc);
+    }
     if (lane == 0) {
       a.z[row] = acc;
       dotc = acc * rs[row];
@@ -201,12 +233,22 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
   }
 }
 
+// Preconditioner apply with M = Q^{-1} stored as DF pairs.
 cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, double* z,
                             double* sc, int* fl, double* bpart, unsigned* bcnt, int mode,
                             cudaStream_t st) {
   SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, mode, 0.0};
-  const size_t smem = (size_t)m * sizeof(double);
-  { note_launch(); k_symv<<<(m + 7) / 8, 256, smem, st>>>(a); }
+  const size_t smem = (size_t)m * 2 * sizeof(double);
+  { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a); }
+  return cudaGetLastError();
+}
+
+// Product with an FP64 symmetric matrix (Q in the factor's quality check).
+cudaError_t launch_symv_f64(const double* M, int mp, int m, const double* r, double* z,
+                            cudaStream_t st) {
+  SymvArgs a{M, mp, m, r, z, nullptr, nullptr, nullptr, nullptr, SYMV_PLAIN, 0.0};
+  const size_t smem = (size_t)m * 2 * sizeof(double);
+  { note_launch(); k_symv<false><<<(m + 7) / 8, 256, smem, st>>>(a); }
   return cudaGetLastError();
 }
 
@@ -214,15 +256,18 @@ cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, do
                              double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
                              cudaStream_t st) {
   SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, SYMV_CG_INIT, rel_tol * rel_tol};
-  const size_t smem = (size_t)m * sizeof(double);
-  { note_launch(); k_symv<<<(m + 7) / 8, 256, smem, st>>>(a); }
+  const size_t smem = (size_t)m * 2 * sizeof(double);
+  { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a); }
   return cudaGetLastError();
 }
 
 cudaError_t symv_set_smem(int m) {
-  const int bytes = m * (int)sizeof(double);
-  if (bytes > 48 * 1024)
-    return cudaFuncSetAttribute(k_symv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const int bytes = m * 2 * (int)sizeof(double);
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_symv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_symv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  }
   return cudaSuccess;
 }
 

@@ -122,9 +122,9 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->colptr);
   dfree(c->rowidx);
   dfree(c->vals);
-  void* bufs[] = {c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
+  void* bufs[] = {c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
-                  c->dyacc, c->rhs, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->G,
+                  c->dyacc, c->rhs, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->G,
                   c->u, c->Q, c->M, c->X, c->Pinv, c->T, c->C, c->Qsplit, c->sc, c->fl, c->bpart,
                   c->bcnt};
   for (void* p : bufs) dfree(p);
@@ -147,6 +147,7 @@ static lp_status alloc_workspace(lp_ctx* c) {
   const int64_t n = c->n;
   double** nvec[] = {&c->x, &c->s, &c->d2, &c->d, &c->rd, &c->t, &c->wu, &c->dx, &c->ds};
   for (double** p : nvec) LP_TRY(dalloc(p, (size_t)n));
+  LP_TRY(dalloc(&c->d2f, (size_t)n));
   double** mvec[] = {&c->y, &c->rp, &c->p, &c->dy, &c->r, &c->z, &c->dd, &c->q, &c->rtil,
                      &c->qhat, &c->res, &c->tm, &c->dyacc, &c->rhs};
   for (double** p : mvec) LP_TRY(dalloc(p, (size_t)m));
@@ -158,6 +159,7 @@ static lp_status alloc_workspace(lp_ctx* c) {
   c->w = c->prm.sketch_w ? c->prm.sketch_w : 4 * m;
   LP_TRY(dalloc(&c->hb, (size_t)n * c->ss));
   LP_TRY(dalloc(&c->list, (size_t)n * c->ss));
+  LP_TRY(dalloc(&c->coef, (size_t)n * c->ss));
   LP_TRY(dalloc(&c->cnt, (size_t)c->w + 1));
   LP_TRY(dalloc(&c->start, (size_t)c->w + 1));
   LP_TRY(dalloc(&c->cursor, (size_t)c->w + 1));
@@ -450,6 +452,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     a.n = c->n;
     a.v = v;
     a.d2 = w;
+    a.d2f = (!precise && w == c->d2) ? c->d2f : nullptr;
     a.colout = t;
     a.part = c->part;
     a.fl = c->fl;
@@ -538,7 +541,8 @@ static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* 
 static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, const double* s,
                                double sigma, double* rp, double* rd, double* p) {
   PhaseScope ps(c, LP_PH_RESIDUALS);
-  LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, sigma, c->c, c->st));
+  LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, sigma, c->c, c->st,
+                            c->d2f));
   int nblk;
   if (!c->sparse) {
     ColArgs a{};
@@ -599,10 +603,11 @@ static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
   LP_CU(cudaMemsetAsync(c->cnt, 0, (c->w + 1) * sizeof(int32_t), c->st));
   LP_CU(launch_sketch_hash(c->prm.seed, k, c->n, c->ss, c->w, c->hb, c->cnt, nullptr, nullptr, c->st));
   LP_CU(launch_sketch_scan(c->cnt, c->w, c->start, c->cursor, c->st));
-  LP_CU(launch_sketch_scatter(c->hb, c->n, c->ss, c->start, c->cursor, c->list, c->st));
+  LP_CU(launch_sketch_scatter(c->hb, c->n, c->ss, c->start, c->cursor, c->list, d, c->coef,
+                              c->st));
   if (!c->sparse) {
     LP_CU(launch_sketch_gather_dense(c->a_dtype, c->A, c->lda, c->m, c->ss, c->w, c->start,
-                                     c->list, d, G, c->ldg, c->st));
+                                     c->list, d, G, c->ldg, c->st, c->coef));
   } else {
     LP_CU(launch_sketch_gather_csc(c->a_dtype, c->colptr, c->rowidx, c->vals, c->m, c->ss, c->w,
                                    c->start, c->list, d, G, c->ldg, c->st));
@@ -619,16 +624,14 @@ static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
   double eps = 0.0;
   for (;;) {
     LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
-    LP_CU(cudaMemcpyAsync(c->M, c->Q, (size_t)c->mp * c->mp * sizeof(double),
-                          cudaMemcpyDeviceToDevice, c->st));
-    if (eps > 0.0) LP_CU(launch_shift_diag(c->M, c->mp, c->m, eps, c->st));
-    LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->fl, c->st));
-    // a-posteriori check on a fixed probe v = 1: ||Q (M v) - v|| / ||v|| must be small
+    LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps, c->fl, c->st));
+    // a-posteriori check on a fixed probe v = 1: ||(Q + eps diag Q)(M v) - v|| / ||v|| must be
+    // small, i.e. M must be an accurate inverse of the (shifted) matrix it was computed from
     LP_CU(launch_vec_ops(VOP_ONES, c->res, nullptr, nullptr, c->m, nullptr, c->st));
     LP_CU(launch_symv_dot(c->M, c->mp, c->m, c->res, c->tm, c->sc, c->fl, c->bpart, c->bcnt,
                           SYMV_PLAIN, c->st));
-    LP_CU(launch_symv_dot(c->Q, c->mp, c->m, c->tm, c->rhs, c->sc, c->fl, c->bpart, c->bcnt,
-                          SYMV_PLAIN, c->st));
+    LP_CU(launch_symv_f64(c->Q, c->mp, c->m, c->tm, c->rhs, c->st));
+    if (eps > 0.0) LP_CU(launch_add_shift(c->rhs, c->Q, c->mp, c->m, eps, c->tm, c->st));
     LP_CU(launch_vec_ops(VOP_SUB, c->rhs, c->rhs, c->res, c->m, nullptr, c->st));
     LP_CU(launch_norm2(c->rhs, c->m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
     LP_TRY(sync_scalars(c));
@@ -860,7 +863,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
   if (!c || !x || !s || !p || !dy) return fail(LP_ERR_ARG, "lp_normal_solve: NULL argument");
   if (k < 0) return fail(LP_ERR_ARG, "lp_normal_solve: k < 0");
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
-                            c->c, c->st));
+                            c->c, c->st, c->d2f));
   LP_TRY(sync_scalars(c));
   const double mu = c->sc_h[SC_MU];
   if (!(mu > 0) || !isfinite(mu)) return fail(LP_ERR_ARG, "lp_normal_solve: x, s must be positive");
@@ -923,7 +926,12 @@ extern "C" lp_status lp_factor(lp_ctx* c, const double* G, double* Q, double* Mi
   LP_TRY(run_factor(c, c->G, false));
   const size_t row = c->m * sizeof(double), pitch = c->mp * sizeof(double);
   if (Q) LP_CU(cudaMemcpy2DAsync(Q, row, c->Q, pitch, row, c->m, cudaMemcpyDefault, c->st));
-  if (Minv) LP_CU(cudaMemcpy2DAsync(Minv, row, c->M, pitch, row, c->m, cudaMemcpyDefault, c->st));
+  if (Minv) {
+    // M is kept as double-float pairs; assemble FP64 entries (device scratch: X)
+    LP_CU(launch_df_to_double(c->M, c->mp, c->m, c->X, c->m, c->st));
+    LP_CU(cudaMemcpyAsync(Minv, c->X, (size_t)c->m * c->m * sizeof(double), cudaMemcpyDefault,
+                          c->st));
+  }
   LP_CU(cudaStreamSynchronize(c->st));
   return LP_OK;
 }
@@ -950,7 +958,7 @@ extern "C" lp_status lp_step(lp_ctx* c, double* x, double* y, double* s, const d
   if (!c || !x || !y || !s || !rd || !dy || !Atdy || !Wu) return fail(LP_ERR_ARG, "lp_step: NULL argument");
   if (!(mu0 > 0)) return fail(LP_ERR_ARG, "lp_step: mu0 must be positive");
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
-                            c->c, c->st));
+                            c->c, c->st, c->d2f));
   (void)mu;  // mu is recomputed from x and s on the device
   LP_TRY(run_step(c, x, y, s, rd, dy, Atdy, Wu, eta, mu0, dx ? dx : c->dx, ds ? ds : c->ds));
   LP_TRY(sync_scalars(c));

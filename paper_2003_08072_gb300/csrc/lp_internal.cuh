@@ -92,6 +92,7 @@ struct lp_ctx {
   // n-vectors
   double *x = nullptr, *y = nullptr, *s = nullptr, *d2 = nullptr, *d = nullptr;
   double *rd = nullptr, *t = nullptr, *wu = nullptr, *dx = nullptr, *ds = nullptr;
+  float* d2f = nullptr;        // D^2 rounded to FP32 for the FP32-accumulated CG product
   // m-vectors
   double *rp = nullptr, *p = nullptr, *dy = nullptr, *r = nullptr, *z = nullptr, *dd = nullptr;
   double *q = nullptr, *rtil = nullptr, *qhat = nullptr, *res = nullptr, *tm = nullptr;
@@ -108,6 +109,7 @@ struct lp_ctx {
   int32_t* start = nullptr;    // w + 1
   int32_t* cursor = nullptr;   // w
   int32_t* list = nullptr;     // n*s entries: column | sign bit 31
+  float2* coef = nullptr;      // n*s entries: sign d_i / sqrt(s) as a double-float pair
   double* G = nullptr;         // m x w column-major, leading dimension ldg (even)
   int ldg = 0;
   double* u = nullptr;         // w
@@ -115,7 +117,7 @@ struct lp_ctx {
   // factor
   int mp = 0;                  // m rounded up to kNB
   double* Q = nullptr;         // mp x mp row-major (full symmetric)
-  double* M = nullptr;         // Q^{-1}, mp x mp row-major (full symmetric)
+  double* M = nullptr;         // Q^{-1} as double-float pairs (hi, lo: two mp x mp float matrices)
   double* X = nullptr;         // L^{-1} work buffer of the factor, mp x mp
   double* Pinv = nullptr;      // kNB x kNB
   double* T = nullptr;         // kNB x mp
@@ -170,6 +172,7 @@ struct ColArgs {
   int64_t ntiles;
   const double* v;     // m-vector for the column dots
   const double* d2;    // NORMAL: per-column weight (NULL = 1)
+  const float* d2f;    // NORMAL with FP32 accumulation: the same weight rounded to FP32 (optional)
   const double* x;     // RESID
   const double* s;     // RESID
   const double* c;     // RESID
@@ -228,7 +231,7 @@ cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st);
 // n-vector kernels
 cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
                                 double* sc, double* bpart, unsigned* bcnt, double sigma,
-                                const double* c, cudaStream_t st);
+                                const double* c, cudaStream_t st, float* d2f = nullptr);
 cudaError_t launch_norm2(const double* v, int64_t n, double* sc, int slot, double* bpart,
                          unsigned* bcnt, cudaStream_t st);
 
@@ -238,10 +241,12 @@ cudaError_t launch_sketch_hash(uint64_t seed, int k, int64_t n, int s, int w, in
 cudaError_t launch_sketch_scan(const int32_t* cnt, int w, int32_t* start, int32_t* cursor,
                                cudaStream_t st);
 cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, const int32_t* start,
-                                  int32_t* cursor, int32_t* list, cudaStream_t st);
+                                  int32_t* cursor, int32_t* list, const double* d, float2* coef,
+                                  cudaStream_t st);
 cudaError_t launch_sketch_gather_dense(lp_dtype ta, const void* A, int64_t lda, int m, int s,
                                        int w, const int32_t* start, const int32_t* list,
-                                       const double* d, double* G, int ldg, cudaStream_t st);
+                                       const double* d, double* G, int ldg, cudaStream_t st,
+                                       const float2* coef = nullptr);
 cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const int32_t* rowidx,
                                      const void* vals, int m, int s, int w, const int32_t* start,
                                      const int32_t* list, const double* d, double* G, int ldg,
@@ -251,8 +256,14 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
 cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* Q, double* Qsplit,
                         int split, cudaStream_t st);
 cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t st);
-cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int* fl,
+cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double eps,
+                             const double* v, cudaStream_t st);
+cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
+                                int* fl, cudaStream_t st);
+cudaError_t launch_df_to_double(const double* Mdf, int mp, int m, double* out, int ld,
                                 cudaStream_t st);
+cudaError_t launch_symv_f64(const double* M, int mp, int m, const double* r, double* z,
+                            cudaStream_t st);
 
 // CG / preconditioner
 cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, double* z,
