@@ -206,6 +206,16 @@ __device__ __forceinline__ void df_fma(float a, float bh, float bl, float& s, fl
   c += (e + pe) + a * bl;
 }
 
+// (s, c) += (ah + al) * (bh + bl)
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& s, float& c) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = fmaf(ah, bh, -p);
+  float t, e;
+  two_sum(s, p, t, e);
+  s = t;
+  c += (e + pe) + fmaf(ah, bl, al * bh);
+}
+
 // (s1, c1) += (s2, c2), renormalised
 __device__ __forceinline__ void df_add(float& s1, float& c1, float s2, float c2) {
   float t, e;

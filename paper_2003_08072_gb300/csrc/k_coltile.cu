@@ -39,7 +39,16 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int row = rowb[sl] + e;
-      vr[sl][e] = (rok[sl] && row < a.m) ? (ACC)a.v[row] : (ACC)0;
+      double vv = 0.0;
+      if (rok[sl] && row < a.m) {
+        if (a.dz) {   // fused CG direction update d = z + beta d_old
+          vv = fma(a.sc[SC_BETA], a.dold[row], a.dz[row]);
+          if (blockIdx.x == 0) a.dnew[row] = vv;
+        } else {
+          vv = a.v[row];
+        }
+      }
+      vr[sl][e] = (ACC)vv;
 #pragma unroll
       for (int o = 0; o < NOUT; ++o) yr[o][sl][e] = (ACC)0;
     }
@@ -130,6 +139,47 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
 #pragma unroll
           for (int e = 0; e < VEC; ++e) yr[o][sl][e] = fma(cc[o], av[e], yr[o][sl][e]);
       }
+    }
+  }
+  if constexpr (MODE == MODE_NORMAL && std::is_same<ACC, float>::value) {
+    if (a.qacc) {
+      // kQCopies copies of q spread the atomic traffic over more L2 lines
+      float* qc = a.qacc + (size_t)(blockIdx.x % kQCopies) * a.m;
+#pragma unroll
+      for (int sl = 0; sl < SPW; ++sl)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const int row = rowb[sl] + e;
+          if (rok[sl] && row < a.m) atomicAdd(&qc[row], yr[0][sl][e]);
+        }
+      // last CTA: d^T q and alpha (no waiting: the last CTA to arrive does the work)
+      __shared__ bool s_last;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = (atomicAdd(a.cnt, 1u) == gridDim.x - 1);
+      __syncthreads();
+      if (!s_last) return;
+      __threadfence();
+      double dq[1] = {0.0};
+      for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
+        float qi = 0.f;
+#pragma unroll
+        for (int k = 0; k < kQCopies; ++k) qi += __ldcg(&a.qacc[(size_t)k * a.m + i]);
+        dq[0] += a.dnew[i] * (double)qi;
+      }
+      block_sum<1>(dq);
+      if (threadIdx.x == 0) {
+        *a.cnt = 0u;
+        a.scw[SC_DQ] = dq[0];
+        if (!(dq[0] > 0.0) || !isfinite(dq[0])) {
+          a.flw[FL_NUMERIC] = 1;
+          a.flw[FL_DONE] = 1;
+          a.scw[SC_ALPHA] = 0.0;
+        } else {
+          a.scw[SC_ALPHA] = a.scw[SC_RHO] / dq[0];
+        }
+      }
+      return;
     }
   }
   ACC* part = reinterpret_cast<ACC*>(a.part);

@@ -66,17 +66,27 @@ __global__ void __launch_bounds__(512) k_coltile_df(ColArgs a) {
   const float* A = reinterpret_cast<const float*>(a.A);
   const int cl = lane % TILE;
   int it = 0;
+  // software pipeline: the next tile's columns are loaded while the current one is computed
+  uint4 an[TILE][SPW];
+  auto load_tile = [&](int64_t tl, uint4 (&dst)[TILE][SPW]) {
+#pragma unroll
+    for (int c = 0; c < TILE; ++c) {
+      const int64_t col = tl * TILE + c;
+#pragma unroll
+      for (int sl = 0; sl < SPW; ++sl)
+        dst[c][sl] = (tl < a.ntiles && col < a.n && rok[sl]) ? ld_stream(A + col * a.lda + rowb[sl])
+                                                             : make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  load_tile(blockIdx.x, an);
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
     const int64_t col0 = tile * TILE;
     uint4 ar[TILE][SPW];
 #pragma unroll
-    for (int c = 0; c < TILE; ++c) {
-      const int64_t col = col0 + c;
+    for (int c = 0; c < TILE; ++c)
 #pragma unroll
-      for (int sl = 0; sl < SPW; ++sl)
-        ar[c][sl] = (col < a.n && rok[sl]) ? ld_stream(A + col * a.lda + rowb[sl])
-                                           : make_uint4(0u, 0u, 0u, 0u);
-    }
+      for (int sl = 0; sl < SPW; ++sl) ar[c][sl] = an[c][sl];
+    load_tile(tile + gridDim.x, an);
     const int64_t mycol = col0 + cl;
     const bool cok = mycol < a.n;
     double pc0 = 0.0, pc1 = 1.0, pc2 = 0.0;

@@ -16,7 +16,14 @@ __global__ void __launch_bounds__(512) k_csc(CscArgs a) {
   ACC* ys = vs + a.m;
   const TV* vals = reinterpret_cast<const TV*>(a.vals);
   for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
-    vs[i] = (ACC)a.v[i];
+    double vv;
+    if (a.dz) {   // fused CG direction update d = z + beta d_old
+      vv = fma(a.sc[SC_BETA], a.dold[i], a.dz[i]);
+      if (blockIdx.x == 0) a.dnew[i] = vv;
+    } else {
+      vv = a.v[i];
+    }
+    vs[i] = (ACC)vv;
 #pragma unroll
     for (int o = 0; o < NOUT; ++o) ys[o * a.m + i] = (ACC)0;
   }

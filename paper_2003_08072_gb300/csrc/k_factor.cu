@@ -197,14 +197,6 @@ struct DFTile {
   float l[kNB][kNB + 1];
 };
 
-__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& s, float& c) {
-  const float p = __fmul_rn(ah, bh);
-  const float pe = fmaf(ah, bh, -p);
-  float t, e;
-  two_sum(s, p, t, e);
-  s = t;
-  c += (e + pe) + fmaf(ah, bl, al * bh);
-}
 
 __device__ __forceinline__ void load_df(DFTile& T, const float* h, const float* l, size_t off, int ld) {
   for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
@@ -273,7 +265,9 @@ __device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl
       T.l[tid][p] = l;
     }
     __syncthreads();
-    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < (kNB * kNB) / 256; ++k) {
+      const int e = tid + 256 * k;
       const int i = e / kNB, j = e % kNB;
       if (j > p && j <= i) {
         float h, l;

@@ -153,6 +153,13 @@ struct SymvArgs {
   unsigned* bcnt;
   int mode;
   double rel2;     // CG relative tolerance squared (CG_INIT)
+  // fused residual update (CG_STEP): r = rold - alpha q; CTA 0 stores r and dy += alpha d
+  const double* rold;
+  const double* q;
+  const double* d;
+  double* dy;
+  const float* qf;     // q accumulated in FP32 (instead of q)
+  float* qzero;        // zeroed by CTA 0 for the next CG product
 };
 
 // DF: M holds double-float pairs (Mh = (float*)M, Ml = Mh + mp^2) and the row sums run on the
@@ -161,10 +168,35 @@ template <bool DF>
 __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
   if (a.mode == SYMV_CG_STEP && a.fl[FL_DONE]) return;
   extern __shared__ double rs[];
-  float* rh = reinterpret_cast<float*>(rs + a.m);   // DF: r split into hi / lo floats
-  float* rl = rh + a.m;
-  for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
-    const double v = a.r[i];
+  const int m4 = (a.m + 3) & ~3;                      // rows of M are padded (mp >= m4)
+  float* rh = reinterpret_cast<float*>(rs + m4);      // DF: r split into hi / lo floats
+  float* rl = rh + m4;
+  const double al = a.rold ? a.sc[SC_ALPHA] : 0.0;
+  for (int i = threadIdx.x; i < m4; i += blockDim.x) {
+    double v = 0.0;
+    if (i < a.m) {
+      if (a.rold) {
+        double qi;
+        if (a.qf) {
+          float qs = 0.f;
+#pragma unroll
+          for (int k = 0; k < kQCopies; ++k) qs += a.qf[(size_t)k * a.m + i];
+          qi = (double)qs;
+        } else {
+          qi = a.q[i];
+        }
+        v = fma(-al, qi, a.rold[i]);
+        if (blockIdx.x == 0) {
+          const_cast<double*>(a.r)[i] = v;
+          a.dy[i] = fma(al, a.d[i], a.dy[i]);
+          if (a.qzero)
+#pragma unroll
+            for (int k = 0; k < kQCopies; ++k) a.qzero[(size_t)k * a.m + i] = 0.f;
+        }
+      } else {
+        v = a.r[i];
+      }
+    }
     rs[i] = v;
     if (DF) split_double(v, rh[i], rl[i]);
   }
@@ -175,17 +207,23 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
   if (row < a.m) {
     double acc;
     if constexpr (DF) {
-      const float* Mh = reinterpret_cast<const float*>(a.M) + (size_t)row * a.mp;
-      const float* Ml = Mh + (size_t)a.mp * a.mp;
+      // 16-byte loads of the row's hi and lo parts: every load of a row is in flight at once
+      const float4* Mh = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.M) +
+                                                         (size_t)row * a.mp);
+      const float4* Ml = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.M) +
+                                                         (size_t)a.mp * a.mp + (size_t)row * a.mp);
+      const float4* rh4 = reinterpret_cast<const float4*>(rh);
+      const float4* rl4 = reinterpret_cast<const float4*>(rl);
+      const int n4 = m4 >> 2;
       float s = 0.f, c = 0.f;
-      for (int j = lane; j < a.m; j += 32) {
-        const float mh = Mh[j], ml = Ml[j];
-        const float p = __fmul_rn(mh, rh[j]);
-        const float pe = fmaf(mh, rh[j], -p);
-        float t, e;
-        two_sum(s, p, t, e);
-        s = t;
-        c += (e + pe) + fmaf(mh, rl[j], ml * rh[j]);
+#pragma unroll 4
+      for (int j = lane; j < n4; j += 32) {
+        const float4 mh = __ldcg(Mh + j), ml = __ldcg(Ml + j);
+        const float4 xh = rh4[j], xl = rl4[j];
+        df_mac(mh.x, ml.x, xh.x, xl.x, s, c);
+        df_mac(mh.y, ml.y, xh.y, xl.y, s, c);
+        df_mac(mh.z, ml.z, xh.z, xl.z, s, c);
+        df_mac(mh.w, ml.w, xh.w, xl.w, s, c);
       }
 #pragma unroll
       for (int off = 16; off >= 1; off >>= 1)
@@ -237,8 +275,19 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
 cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, double* z,
                             double* sc, int* fl, double* bpart, unsigned* bcnt, int mode,
                             cudaStream_t st) {
-  SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, mode, 0.0};
-  const size_t smem = (size_t)m * 2 * sizeof(double);
+  SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, mode, 0.0, nullptr, nullptr, nullptr, nullptr,
+             nullptr, nullptr};
+  const size_t smem = (size_t)((m + 3) & ~3) * 2 * sizeof(double);
+  { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* rold,
+                                const double* q, const double* d, double* dy, double* rnew,
+                                double* z, double* sc, int* fl, double* bpart, unsigned* bcnt,
+                                cudaStream_t st, const float* qf, float* qzero) {
+  SymvArgs a{M, mp, m, rnew, z, sc, fl, bpart, bcnt, SYMV_CG_STEP, 0.0, rold, q, d, dy, qf, qzero};
+  const size_t smem = (size_t)((m + 3) & ~3) * 2 * sizeof(double);
   { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a); }
   return cudaGetLastError();
 }
@@ -246,8 +295,9 @@ cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, dou
 // Product with an FP64 symmetric matrix (Q in the factor's quality check).
 cudaError_t launch_symv_f64(const double* M, int mp, int m, const double* r, double* z,
                             cudaStream_t st) {
-  SymvArgs a{M, mp, m, r, z, nullptr, nullptr, nullptr, nullptr, SYMV_PLAIN, 0.0};
-  const size_t smem = (size_t)m * 2 * sizeof(double);
+  SymvArgs a{M, mp, m, r, z, nullptr, nullptr, nullptr, nullptr, SYMV_PLAIN, 0.0,
+             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const size_t smem = (size_t)((m + 3) & ~3) * 2 * sizeof(double);
   { note_launch(); k_symv<false><<<(m + 7) / 8, 256, smem, st>>>(a); }
   return cudaGetLastError();
 }
@@ -255,14 +305,15 @@ cudaError_t launch_symv_f64(const double* M, int mp, int m, const double* r, dou
 cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, double* z,
                              double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
                              cudaStream_t st) {
-  SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, SYMV_CG_INIT, rel_tol * rel_tol};
-  const size_t smem = (size_t)m * 2 * sizeof(double);
+  SymvArgs a{M, mp, m, r, z, sc, fl, bpart, bcnt, SYMV_CG_INIT, rel_tol * rel_tol,
+             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const size_t smem = (size_t)((m + 3) & ~3) * 2 * sizeof(double);
   { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a); }
   return cudaGetLastError();
 }
 
 cudaError_t symv_set_smem(int m) {
-  const int bytes = m * 2 * (int)sizeof(double);
+  const int bytes = ((m + 3) & ~3) * 2 * (int)sizeof(double);
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_symv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;

@@ -124,7 +124,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->vals);
   void* bufs[] = {c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
-                  c->dyacc, c->rhs, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->G,
+                  c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G,
                   c->u, c->Q, c->M, c->X, c->Pinv, c->T, c->C, c->Qsplit, c->sc, c->fl, c->bpart,
                   c->bcnt};
   for (void* p : bufs) dfree(p);
@@ -149,7 +149,7 @@ static lp_status alloc_workspace(lp_ctx* c) {
   for (double** p : nvec) LP_TRY(dalloc(p, (size_t)n));
   LP_TRY(dalloc(&c->d2f, (size_t)n));
   double** mvec[] = {&c->y, &c->rp, &c->p, &c->dy, &c->r, &c->z, &c->dd, &c->q, &c->rtil,
-                     &c->qhat, &c->res, &c->tm, &c->dyacc, &c->rhs};
+                     &c->qhat, &c->res, &c->tm, &c->dyacc, &c->rhs, &c->r_alt, &c->d_alt};
   for (double** p : mvec) LP_TRY(dalloc(p, (size_t)m));
   const int maxgrid = std::max(coltile_max_grid(c->num_sms), csc_max_grid(c->num_sms));
   c->part_bytes = (size_t)maxgrid * 2 * m * sizeof(double);
@@ -160,6 +160,7 @@ static lp_status alloc_workspace(lp_ctx* c) {
   LP_TRY(dalloc(&c->hb, (size_t)n * c->ss));
   LP_TRY(dalloc(&c->list, (size_t)n * c->ss));
   LP_TRY(dalloc(&c->coef, (size_t)n * c->ss));
+  LP_TRY(dalloc(&c->qf, (size_t)2 * kQCopies * m));
   LP_TRY(dalloc(&c->cnt, (size_t)c->w + 1));
   LP_TRY(dalloc(&c->start, (size_t)c->w + 1));
   LP_TRY(dalloc(&c->cursor, (size_t)c->w + 1));
@@ -438,7 +439,9 @@ extern "C" lp_status lp_set_params(lp_ctx* c, const lp_params* prm) {
 // precise: master copy with FP64 accumulation; else the streamed copy.
 static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const double* w, double* t,
                              int red_mode, double* out, const double* p0, int skip_if_done,
-                             bool record_mv = false) {
+                             bool record_mv = false, const double* dz = nullptr,
+                             const double* dold = nullptr, double* dnew = nullptr,
+                             float* qacc = nullptr) {
   int nblk;
   bool acc64;
   cudaEvent_t ea = nullptr, eb = nullptr;
@@ -456,8 +459,20 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     a.colout = t;
     a.part = c->part;
     a.fl = c->fl;
+    a.sc = c->sc;
     a.skip_if_done = skip_if_done;
+    a.dz = dz;
+    a.dold = dold;
+    a.dnew = dnew;
     acc64 = precise || ta == LP_F64;
+    if (qacc && !acc64) {
+      a.qacc = qacc;
+      a.cnt = c->bcnt + 1;
+      a.scw = c->sc;
+      a.flw = c->fl;
+    } else {
+      qacc = nullptr;
+    }
     nblk = launch_coltile(ta, acc64, MODE_NORMAL, a, c->num_sms, c->st);
   } else {
     CscArgs a{};
@@ -472,7 +487,11 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     a.colout = t;
     a.part = c->part;
     a.fl = c->fl;
+    a.sc = c->sc;
     a.skip_if_done = skip_if_done;
+    a.dz = dz;
+    a.dold = dold;
+    a.dnew = dnew;
     acc64 = precise || tv == LP_F64;
     nblk = launch_csc(tv, acc64, MODE_NORMAL, a, c->num_sms, c->st);
   }
@@ -482,6 +501,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
   }
   if (nblk < 0) return fail(LP_ERR_ARG, "unsupported shape for the matrix pass");
   LP_CU(cudaGetLastError());
+  if (qacc) return LP_OK;   // reduced by the kernel itself
   RedArgs r{};
   r.mode = red_mode;
   r.part = c->part;
@@ -491,7 +511,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
   r.acc_f64 = acc64;
   r.out0 = out;
   r.p0 = p0;
-  r.dvec = v;
+  r.dvec = dnew ? dnew : v;
   r.sc = c->sc;
   r.fl = c->fl;
   r.bpart = c->bpart;
@@ -504,7 +524,9 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
 // Product with the sketch Q v = G G^T v in FP64, u = G^T v (optional), reduced by red_mode:
 // RED_MINUS_P: out = Q v - p0;  RED_PLAIN: out = Q v;  RED_CG_Q: out = q = Q v and d^T q.
 static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* u, double* out,
-                           const double* p0, int red_mode, int skip_if_done) {
+                           const double* p0, int red_mode, int skip_if_done,
+                           const double* dz = nullptr, const double* dold = nullptr,
+                           double* dnew = nullptr) {
   ColArgs a{};
   a.A = G;
   a.lda = c->ldg;
@@ -515,7 +537,11 @@ static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* 
   a.colout = u;
   a.part = c->part;
   a.fl = c->fl;
+  a.sc = c->sc;
   a.skip_if_done = skip_if_done;
+  a.dz = dz;
+  a.dold = dold;
+  a.dnew = dnew;
   const int nblk = launch_coltile(LP_F64, true, MODE_NORMAL, a, c->num_sms, c->st);
   if (nblk < 0) return fail(LP_ERR_ARG, "unsupported shape for the sketch pass");
   RedArgs r{};
@@ -527,7 +553,7 @@ static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* 
   r.acc_f64 = true;
   r.out0 = out;
   r.p0 = p0;
-  r.dvec = v;
+  r.dvec = dnew ? dnew : v;
   r.sc = c->sc;
   r.fl = c->fl;
   r.bpart = c->bpart;
@@ -661,18 +687,31 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
   LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_NUMERIC, 0, c->st));
   LP_CU(launch_symv_init(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt, rel_tol,
                          c->st));
-  LP_CU(launch_vec_ops(VOP_COPY, c->dd, c->z, nullptr, m, nullptr, c->st));
+  // d starts at 0 so that the first fused direction update (beta = 0) gives d = z
+  LP_CU(launch_vec_ops(VOP_ZERO, c->d_alt, nullptr, nullptr, m, nullptr, c->st));
+  // iteration j: d_j = z + beta d_{j-1} into dbuf[j & 1]; r_{j+1} into rbuf[(j + 1) & 1]
+  double* rbuf[2] = {c->r, c->r_alt};
+  double* dbuf[2] = {c->dd, c->d_alt};
+  // FP32-accumulated dense products reduce themselves into qbuf with atomics
+  const bool atomic_q = (op == 0) && !c->sparse && c->s_dtype != LP_F64;
+  float* qbuf[2] = {c->qf, c->qf + (size_t)kQCopies * m};
+  if (atomic_q) LP_CU(cudaMemsetAsync(c->qf, 0, (size_t)kQCopies * m * sizeof(float), c->st));
   int done_before = 0;
+  int j = 0;
   for (;;) {
-    for (int b = 0; b < c->prm.cg_batch; ++b) {
+    for (int b = 0; b < c->prm.cg_batch; ++b, ++j) {
+      double* dnew = dbuf[j & 1];
+      const double* dold = dbuf[(j + 1) & 1];
       if (op == 0)
-        LP_TRY(pass_normal(c, false, c->dd, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1, true));
+        LP_TRY(pass_normal(c, false, nullptr, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1, true,
+                           c->z, dold, dnew, atomic_q ? qbuf[j & 1] : nullptr));
       else
-        LP_TRY(pass_gram(c, c->G, c->dd, nullptr, c->q, nullptr, RED_CG_Q, 1));
-      LP_CU(launch_cg_axpy(delta, c->r, c->dd, c->q, m, c->sc, c->fl, c->st));
-      LP_CU(launch_symv_dot(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt,
-                            SYMV_CG_STEP, c->st));
-      LP_CU(launch_cg_dir(c->dd, c->z, m, c->sc, c->fl, c->st));
+        LP_TRY(pass_gram(c, c->G, nullptr, nullptr, c->q, nullptr, RED_CG_Q, 1, c->z, dold,
+                         dnew));
+      LP_CU(launch_symv_cg_step(c->M, c->mp, m, rbuf[j & 1], c->q, dnew, delta,
+                                rbuf[(j + 1) & 1], c->z, c->sc, c->fl, c->bpart, c->bcnt, c->st,
+                                atomic_q ? qbuf[j & 1] : nullptr,
+                                atomic_q ? qbuf[(j + 1) & 1] : nullptr));
     }
     LP_TRY(sync_scalars(c));
     if (!c->mv_pending.empty()) prof_harvest_mv(c, c->fl_h[FL_ITERS] - done_before);

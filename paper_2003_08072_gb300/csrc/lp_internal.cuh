@@ -54,7 +54,8 @@ enum Flag {
 extern std::atomic<long long> g_launches;   // kernel launches issued (lp_api.cu)
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-constexpr int kNB = 32;          // block size of the Gauss-Jordan inverse
+constexpr int kNB = 32;          // block size of the blocked Cholesky inverse
+constexpr int kQCopies = 8;      // copies of the atomically accumulated CG product
 constexpr int kMaxRedBlocks = 1024;
 
 }  // namespace lpk
@@ -97,6 +98,8 @@ struct lp_ctx {
   double *rp = nullptr, *p = nullptr, *dy = nullptr, *r = nullptr, *z = nullptr, *dd = nullptr;
   double *q = nullptr, *rtil = nullptr, *qhat = nullptr, *res = nullptr, *tm = nullptr;
   double *dyacc = nullptr, *rhs = nullptr;
+  double *r_alt = nullptr, *d_alt = nullptr;   // second buffers of the CG residual / direction
+  float* qf = nullptr;         // 2 x m: atomically accumulated CG products (FP32 streams)
 
   // per-CTA partials of the column-tile kernels
   void* part = nullptr;
@@ -181,6 +184,17 @@ struct ColArgs {
   void* part;          // [grid][nout][m] partials (accumulator type)
   const int* fl;       // skip everything when fl[FL_DONE] != 0 and skip_if_done
   int skip_if_done;
+  // CG direction update fused into the product: v = dz + beta dold (beta = sc[SC_BETA]); CTA 0
+  // stores v into dnew.  Used when dz != NULL.
+  const double* dz;
+  const double* dold;
+  double* dnew;
+  // CG with FP32 accumulation: add the row sums into qacc with atomics instead of writing
+  // partials; the last CTA forms d^T q (d = dnew) and alpha = rho / d^T q in scw / flw.
+  float* qacc;
+  unsigned* cnt;
+  double* scw;
+  int* flw;
 };
 
 // Dense column-tile pass.  acc_f64 selects FP64 accumulation (else FP32).
@@ -204,6 +218,9 @@ struct CscArgs {
   void* part;          // [grid][nout][m]
   const int* fl;
   int skip_if_done;
+  const double* dz;    // fused CG direction update, as in ColArgs
+  const double* dold;
+  double* dnew;
 };
 int launch_csc(lp_dtype tv, bool acc_f64, int mode, CscArgs a, int num_sms, cudaStream_t st);
 
@@ -270,6 +287,13 @@ cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, dou
                             double* sc, int* fl, double* bpart, unsigned* bcnt, int mode,
                             cudaStream_t st);
 enum SymvMode { SYMV_PLAIN = 0, SYMV_CG_INIT = 1, SYMV_CG_STEP = 2, SYMV_F2 = 3 };
+// CG step with the residual update fused: r_new = r_old - alpha q staged by every CTA, stored by
+// CTA 0 with dy += alpha d; then z = M r_new, rho = r_new^T z and the CG bookkeeping.
+cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* rold,
+                                const double* q, const double* d, double* dy, double* rnew,
+                                double* z, double* sc, int* fl, double* bpart, unsigned* bcnt,
+                                cudaStream_t st, const float* qf = nullptr,
+                                float* qzero = nullptr);
 cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, double* z,
                              double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
                              cudaStream_t st);
