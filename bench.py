@@ -29,10 +29,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # DRAM bytes of one CG product launch from an ncu capture of the same kernel source
-# (k_coltile.cu at the recorded hash); reported only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha1": "bf67889fc014d48c8dc7e02a00e34c6a2e1b3c2a",
-               "bytes_per_launch": 804.47e6,
-               "case": "dense m=1000 n=200000 FP32, ncu --set full (profiles/k_coltile_cg_product_"
+# (k_cgprod.cu at the recorded hash); reported only while the kernel source is unchanged.
+NCU_TRAFFIC = {"source_sha1": "",
+               "bytes_per_launch": None,
+               "case": "dense m=1000 n=200000 FP32, ncu --set full (profiles/k_cgprod_cg_product_"
                        "dense_m1000_n200000_f32.md)"}
 
 
@@ -42,8 +42,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--m", type=int, default=1000)
-    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--workload", choices=["dense", "sparse", "scaled"], default="dense",
+                    help="dense: Gaussian m x n; sparse: CSR with --nnz-per-col nonzeros per "
+                         "column; scaled: dense with column scales 10^U(-3,3)")
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--nnz-per-col", type=int, default=8)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--stream", choices=["same", "f32", "bf16", "f16"], default="same")
     ap.add_argument("--sketch-s", type=int, default=4)
@@ -52,7 +56,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=20_000)
     ap.add_argument("--cpu-sample-iters", type=int, default=4)
-    return ap.parse_args()
+    args = ap.parse_args()
+    defaults = {"dense": (1000, 200_000), "sparse": (5000, 2_000_000), "scaled": (2000, 500_000)}
+    dm, dn = defaults[args.workload]
+    args.m = args.m or dm
+    args.n = args.n or dn
+    return args
 
 
 # --------------------------------------------------------------------------- distributed
@@ -166,14 +175,31 @@ def read_peaks():
 
 
 def kernel_sha1():
-    path = os.path.join(ROOT, "paper_2003_08072_gb300", "csrc", "k_coltile.cu")
+    path = os.path.join(ROOT, "paper_2003_08072_gb300", "csrc", "k_cgprod.cu")
     with open(path, "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
 def workload_name(args):
-    return (f"dense Gaussian LP m={args.m} n={args.n} A {args.dtype.upper()} "
+    if args.workload == "sparse":
+        return (f"sparse LP m={args.m} n={args.n}, {args.nnz_per_col} nonzeros per column (CSR, "
+                f"FP32 values, int32 columns), feasible by construction, Algorithm 2 to scaled "
+                f"KKT 1e-8")
+    kind = "dense Gaussian" if args.workload == "dense" else "dense Gaussian, column scales 10^U(-3,3),"
+    return (f"{kind} LP m={args.m} n={args.n} A {args.dtype.upper()} "
             f"(feasible by construction), Algorithm 2 to scaled KKT 1e-8")
+
+
+def make_lp(args):
+    import numpy as np
+
+    import synth
+
+    if args.workload == "sparse":
+        return synth.sparse_lp(0, args.m, args.n, nnz_per_col=args.nnz_per_col)
+    np_dt = np.float32 if args.dtype == "f32" else np.float64
+    scale = (-3, 3) if args.workload == "scaled" else None
+    return synth.dense_lp(0, args.m, args.n, dtype=np_dt, col_scale=scale)
 
 
 def cpu_threads():
@@ -198,8 +224,13 @@ def oracle_sample(args, iters_per_lp: float):
     from oracle import iipm
 
     ns = min(args.cpu_sample_n, args.n)
-    lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64)
-    A = lp.A.astype(np.float64)
+    if args.workload == "sparse":
+        lp = synth.sparse_lp(0, args.m, ns, nnz_per_col=args.nnz_per_col)
+        A = lp.to_scipy()
+    else:
+        lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64,
+                            col_scale=(-3, 3) if args.workload == "scaled" else None)
+        A = lp.A.astype(np.float64)
     prm = iipm.Params(ipm_max_iter=args.cpu_sample_iters, sketch_s=args.sketch_s)
     t0 = time.perf_counter()
     r = iipm.ipm_solve(A, lp.b, lp.c, prm)
@@ -228,22 +259,29 @@ def run_ours(args, rank, world, local):
     pkg.load(build_if_missing=False)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    np_dt = np.float32 if args.dtype == "f32" else np.float64
-    lp = synth.dense_lp(0, args.m, args.n, dtype=np_dt)
+    lp = make_lp(args)
     prm = pkg.lp_params_default()
     prm.sketch_s = args.sketch_s
     prm.cg_batch = args.cg_batch
-    sd = args.dtype if args.stream == "same" else args.stream
-    prm.stream_dtype = pkg.DTYPE_CODES[sd]
-    a_code = pkg.LP_F32 if args.dtype == "f32" else pkg.LP_F64
+    sparse = args.workload == "sparse"
+    sd = (args.dtype if not sparse else "f32") if args.stream == "same" else args.stream
+    prm.stream_dtype = pkg.DTYPE_CODES[sd] if not sparse else pkg.LP_F64
+    a_code = pkg.LP_F32 if (args.dtype == "f32" or sparse) else pkg.LP_F64
     stream = torch.cuda.current_stream(dev)
 
     # ---------------- device-resident runs
-    At_dev = torch.from_numpy(lp.At).to(dev)
     b_dev = torch.from_numpy(lp.b).to(dev)
     c_dev = torch.from_numpy(lp.c).to(dev)
-    ctx = pkg.lp_create(args.m, args.n, pkg.LP_DENSE_COLMAJOR, a_code, At_dev, None, None, 0,
-                        b_dev, c_dev, prm, stream.cuda_stream)
+    if sparse:
+        keep = [torch.from_numpy(v).to(dev) for v in (lp.indptr, lp.indices, lp.values)]
+        ctx = pkg.lp_create(args.m, args.n, pkg.LP_CSR, a_code, keep[2], keep[0], keep[1],
+                            lp.nnz, b_dev, c_dev, prm, stream.cuda_stream)
+        a_bytes = lp.values.nbytes + lp.indices.nbytes + lp.indptr.nbytes
+    else:
+        keep = [torch.from_numpy(lp.At).to(dev)]
+        ctx = pkg.lp_create(args.m, args.n, pkg.LP_DENSE_COLMAJOR, a_code, keep[0], None, None, 0,
+                            b_dev, c_dev, prm, stream.cuda_stream)
+        a_bytes = lp.At.nbytes
     x = torch.empty(args.n, dtype=torch.float64, device=dev)
     y = torch.empty(args.m, dtype=torch.float64, device=dev)
     s = torch.empty(args.n, dtype=torch.float64, device=dev)
@@ -272,13 +310,16 @@ def run_ours(args, rank, world, local):
     pkg.lp_profile_enable(ctx, False)
     obj = float(torch.dot(c_dev, x))
     pkg.lp_destroy(ctx)
-    del At_dev
+    del keep
     torch.cuda.empty_cache()
     t_max = max_over_ranks(elapsed, world)
 
     # ---------------- end to end from host buffers through the C ABI
     k_e2e = args.e2e_steps if args.e2e_steps is not None else args.steps
-    At_h = torch.from_numpy(lp.At).pin_memory()
+    if sparse:
+        host = [torch.from_numpy(v).pin_memory() for v in (lp.indptr, lp.indices, lp.values)]
+    else:
+        host = [torch.from_numpy(lp.At).pin_memory()]
     b_h = torch.from_numpy(lp.b).pin_memory()
     c_h = torch.from_numpy(lp.c).pin_memory()
     xh = torch.empty(args.n, dtype=torch.float64).pin_memory()
@@ -288,13 +329,17 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        cx = pkg.lp_create(args.m, args.n, pkg.LP_DENSE_COLMAJOR, a_code, At_h, None, None, 0,
-                           b_h, c_h, prm, stream.cuda_stream)
+        if sparse:
+            cx = pkg.lp_create(args.m, args.n, pkg.LP_CSR, a_code, host[2], host[0], host[1],
+                               lp.nnz, b_h, c_h, prm, stream.cuda_stream)
+        else:
+            cx = pkg.lp_create(args.m, args.n, pkg.LP_DENSE_COLMAJOR, a_code, host[0], None, None,
+                               0, b_h, c_h, prm, stream.cuda_stream)
         pkg.lp_ipm_solve(cx, xh, yh, sh)
         pkg.lp_destroy(cx)
     torch.cuda.synchronize(dev)
-    e2e_t = max_over_ranks(time.perf_counter() - t0, world)
-    h2d = At_h.numel() * At_h.element_size() + 8 * (args.m + args.n)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world) if k_e2e else float("nan")
+    h2d = a_bytes + 8 * (args.m + args.n)
     d2h = 8 * (2 * args.n + args.m)
 
     if rank != 0:
@@ -303,15 +348,16 @@ def run_ours(args, rank, world, local):
     mv_avg_s = prof.matvec_ms / 1e3 / max(prof.matvec_count, 1)
     achieved = prof.matvec_bytes / mv_avg_s / 1e9 if prof.matvec_count else None
     traffic = None
-    if NCU_TRAFFIC["source_sha1"] == kernel_sha1() and NCU_TRAFFIC["bytes_per_launch"]:
+    if (not sparse and args.workload == "dense" and NCU_TRAFFIC["source_sha1"] == kernel_sha1()
+            and NCU_TRAFFIC["bytes_per_launch"]):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     ipm_iters = statistics.mean(i.ipm_iters for i in infos)
     cg_total = statistics.mean(i.cg_iters_total for i in infos)
     value = world * args.steps / t_max
     line = {
         "metric": "IPM LPs/s (Algorithm 2 to tolerance, dense m=1000 n=200000 FP32 LP)"
-        if (args.m, args.n, args.dtype) == (1000, 200_000, "f32") else
-        f"IPM LPs/s (Algorithm 2 to tolerance, dense m={args.m} n={args.n} {args.dtype})",
+        if (args.workload, args.m, args.n, args.dtype) == ("dense", 1000, 200_000, "f32") else
+        f"IPM LPs/s (Algorithm 2 to tolerance, {args.workload} m={args.m} n={args.n})",
         "value": value,
         "unit": "LP/s",
         "n_gpus": world,
@@ -325,14 +371,15 @@ def run_ours(args, rank, world, local):
         "data": "synthetic",
         "config": {
             "workload": workload_name(args),
-            "m": args.m, "n": args.n, "a_dtype": args.dtype, "stream_dtype": sd,
+            "m": args.m, "n": args.n, "a_dtype": "f32" if sparse else args.dtype,
+            "stream_dtype": sd,
             "sketch": f"sparse sign s={args.sketch_s}, w=4m", "cg_rel_tol": prm.cg_rel_tol,
             "tol": prm.tol, "sigma": prm.sigma, "gamma": prm.gamma,
-            "l2": "inputs larger than L2 (A is %.0f MB)" % (lp.At.nbytes / 1e6),
+            "l2": "inputs larger than L2 (A is %.0f MB)" % (a_bytes / 1e6),
             "parallelism": f"replicas x{world}",
         },
         "roofline": {
-            "kernel": "k_coltile (CG product A D^2 A^T v)",
+            "kernel": ("k_csc" if sparse else "k_cgprod") + " (CG product A D^2 A^T v)",
             "bound": "hbm",
             "achieved": achieved,
             "peak": peak,
@@ -344,7 +391,8 @@ def run_ours(args, rank, world, local):
             "avg_launch_us": 1e6 * mv_avg_s,
             "launches": int(prof.matvec_count),
         },
-        "e2e": {"value": world * k_e2e / e2e_t, "unit": "LP/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": (world * k_e2e / e2e_t) if k_e2e else None, "unit": "LP/s",
+                "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": k_e2e},
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -374,8 +422,14 @@ def oracle_iters_per_lp(args) -> float:
     from oracle import iipm
 
     ns = min(args.cpu_sample_n, args.n)
-    lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64)
-    r = iipm.ipm_solve(lp.A.astype(np.float64), lp.b, lp.c, iipm.Params(), variant="exact")
+    if args.workload == "sparse":
+        lp = synth.sparse_lp(0, args.m, ns, nnz_per_col=args.nnz_per_col)
+        A = lp.to_scipy()
+    else:
+        lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64,
+                            col_scale=(-3, 3) if args.workload == "scaled" else None)
+        A = lp.A.astype(np.float64)
+    r = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(), variant="exact")
     return float(r.iters)
 
 

@@ -69,7 +69,12 @@ typedef struct {
   int32_t sketch_w;      /* sketch width w; 0 = 4m.  Must be a multiple of sketch_s */
   int32_t cg_theory_rule;/* 1: CG also stops only once ||f|| <= gamma sigma sqrt(mu)/(4 sqrt(n)) (Sec. 4) (1) */
   uint64_t seed;         /* W for IPM iteration k is a function of (seed, k) only (0) */
-  lp_dtype stream_dtype; /* dtype A is streamed in by the CG matvec; LP_F64 keeps the input dtype (LP_F64) */
+  lp_dtype stream_dtype; /* dtype A is streamed in by the CG matvec; LP_F64 keeps the input dtype (LP_F64).
+                            Dense LP_BF16 / LP_F16 copies hold column j scaled by a power of two 2^-e_j
+                            (max |entry| in [0.5, 1)), the scales folded into D^2.  A copy below the
+                            input precision is corrected by FP64 refinement; when a refinement round
+                            fails to halve ||f|| (or refine_max rounds pass) the solve streams the
+                            input-precision copy from then on (lp_info.stream_switch_iter). */
   int32_t cg_batch;      /* CG iterations enqueued between host checks of the stop flag (4) */
 } lp_params;
 
@@ -87,6 +92,8 @@ typedef struct {
   double v_norm;           /* ||v|| of the last correction vector (Eq. compv) */
   int32_t status;          /* lp_status of the solve */
   double f_target;         /* CG target of the last solve: min(cg_rel_tol ||f^(0)||, gamma sigma sqrt(mu)/(4 sqrt(n))) */
+  int32_t stream_dtype;    /* lp_dtype the CG products streamed A in at exit (see lp_params.stream_dtype) */
+  int32_t stream_switch_iter; /* IPM iteration at which the solve switched to the master copy; -1 if never */
 } lp_info;
 
 /* Fills *prm with the defaults listed above.  LP_ERR_ARG if prm is NULL. */

@@ -56,6 +56,8 @@ class lp_info(ctypes.Structure):
         ("v_norm", ctypes.c_double),
         ("status", ctypes.c_int32),
         ("f_target", ctypes.c_double),
+        ("stream_dtype", ctypes.c_int32),
+        ("stream_switch_iter", ctypes.c_int32),
     ]
 
     def as_dict(self):

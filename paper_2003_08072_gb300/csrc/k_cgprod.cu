@@ -1,0 +1,457 @@
+// CG product y = A D^2 A^T v (Alg. 1 step 3) over a column-major A streamed below FP64,
+// with FP32 accumulation, A staged through shared memory by bulk asynchronous copies.
+//
+// The register-tiled pass (k_coltile.cu) keeps the column tile it works on in registers, so a
+// CTA cannot load tile t+1 while it reduces tile t, and at large m (or 16-bit types, whose
+// unpacked tile is twice as wide) it runs one CTA per SM with idle gaps between tiles.  Here
+// the CTA is a pipeline: one thread issues cp.async.bulk copies of whole column groups (a group
+// of TC consecutive columns is one contiguous range of TC * lda elements) into a ring of S
+// shared-memory stages, each completing on its own mbarrier, S - 1 groups ahead of the warps
+// that consume them.  A stage is refilled once every warp is past the __syncthreads of the
+// following group, which comes after the last read of the stage.
+//
+// Per group the warps form the TC column dots a_i^T v (rows split across warps as slices of
+// 32 lanes x 16 bytes, v in registers), reduce them across the CTA through shared memory,
+// weight them with D^2 (FP32, times the column scales of a scaled 16-bit copy), and add
+// a_i * coef_i into per-thread row accumulators.  Arithmetic runs on packed pairs of rows
+// (fma.rn.f32x2: half the FMA instructions) when built with LP_CGPROD_PACK=1, and with
+// LP_CGPROD_KEEP=1 a warp with one row slice keeps the unpacked group in registers between
+// the two phases instead of reading and unpacking it twice.  The
+// CTA's row sums then go to the q buffers with atomics (the last CTA forms d^T q and alpha, as
+// in the register-tiled pass) or to per-CTA partials.
+//
+// Every wait on an mbarrier is bounded by the global timer; a wait that gives up sets
+// FL_TIMEOUT and the CTA carries on without the data (the host turns the flag into
+// LP_ERR_TIMEOUT), so no thread leaves early and no copy is left writing into the CTA's
+// shared memory after it exits.
+#include <algorithm>
+
+#include "dev_util.cuh"
+
+namespace lpk {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Global-memory -> shared-memory bulk copy completing on an mbarrier.  dst, src 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Makes mbarrier initialisations visible to the other threads and to the async proxy.
+__device__ __forceinline__ void fence_mbarrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s per wait
+
+// Bounded wait for phase `parity` of bar.  Returns false (after the limit) if it never came.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (unsigned spin = 1;; ++spin) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((spin & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// Packed pairs of FP32 values in one 64-bit register (first value in the low half) and the
+// paired FMA of sm_100 and later: d = a * b + c element by element, each rounded as fmaf.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+
+__device__ __forceinline__ float elem2(uint64_t v, int which) {
+  return __uint_as_float(which ? (unsigned)(v >> 32) : (unsigned)v);
+}
+
+__device__ __forceinline__ float sum2(uint64_t v) { return elem2(v, 0) + elem2(v, 1); }
+
+[[maybe_unused]] __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// 16 bytes of TA -> VEC/2 packed pairs of FP32 (elements 2p, 2p + 1 in pair p).
+template <typename TA>
+__device__ __forceinline__ void unpack_pairs(const uint4& r, uint64_t (&o)[VecN<TA>::N / 2]) {
+  if constexpr (sizeof(TA) == 4) {
+    o[0] = ((uint64_t)r.y << 32) | r.x;
+    o[1] = ((uint64_t)r.w << 32) | r.z;
+  } else {
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if constexpr (std::is_same<TA, __nv_bfloat16>::value) {
+        // a bf16 is the upper half of an FP32
+        o[i] = ((uint64_t)(w[i] & 0xffff0000u) << 32) | (w[i] << 16);
+      } else {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+        o[i] = pack2(f.x, f.y);
+      }
+    }
+  }
+}
+
+// 16 bytes of TA -> VEC FP32 values, or VEC/2 packed pairs
+template <typename TA, bool PACK, typename Acc>
+__device__ __forceinline__ void unpack_acc(const uint4& r, Acc (&o)[PACK ? VecN<TA>::N / 2 : VecN<TA>::N]) {
+  if constexpr (PACK) unpack_pairs<TA>(r, o);
+  else unpack<TA, float>(r, o);
+}
+
+template <bool PACK, typename Acc, int NA>
+__device__ __forceinline__ float acc_elem(const Acc (&y)[NA], int e) {
+  if constexpr (PACK) return elem2(y[e / 2], e & 1);
+  else return y[e];
+}
+
+}  // namespace
+
+// Shared memory: S stages of TC * lda elements, then S mbarriers.
+template <typename TA, int SPW, int TC, bool PACK, bool KEEP>
+__global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroups) {
+  constexpr int VEC = VecN<TA>::N;
+  constexpr int NP = VEC / 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ float red[2][16][TC];
+  __shared__ int s_timeout;
+  if (a.skip_if_done && a.fl[FL_DONE]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const size_t stage_elems = (size_t)TC * a.lda;
+  TA* stages = reinterpret_cast<TA*>(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * stage_elems * sizeof(TA));
+  const TA* A = reinterpret_cast<const TA*>(a.A);
+
+  // groups of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int my_groups =
+      blockIdx.x < ngroups ? (int)((ngroups - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+  const int64_t col_step = (int64_t)gridDim.x * TC;
+  auto issue = [&](int i, int stage) {   // thread 0: copy local group i into a stage
+    const int64_t col0 = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * TC;
+    const int ncols = (int)std::min<int64_t>(TC, a.n - col0);
+    const unsigned bytes = (unsigned)((size_t)ncols * a.lda * sizeof(TA));
+    uint64_t* bar = &bars[stage];
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(stages + (size_t)stage * stage_elems, A + col0 * a.lda, bytes, bar);
+  };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    s_timeout = 0;
+    fence_mbarrier_init();
+    fence_proxy_async_smem();
+    for (int i = 0; i < std::min(S - 1, my_groups); ++i) issue(i, i);
+  }
+
+  // v and the row accumulators: VEC values per slice, as VEC/2 packed pairs with PACK
+  using Acc = typename std::conditional<PACK, uint64_t, float>::type;
+  constexpr int NA = PACK ? NP : VEC;
+  Acc vr[SPW][NA], yr[SPW][NA];
+  int rowb[SPW];
+  bool rok[SPW];
+#pragma unroll
+  for (int sl = 0; sl < SPW; ++sl) {
+    rowb[sl] = ((warp * SPW + sl) * 32 + lane) * VEC;
+    rok[sl] = rowb[sl] < a.m;
+    float vv[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      const int row = rowb[sl] + e;
+      double x = 0.0;
+      if (rok[sl] && row < a.m) {
+        if (a.dz) {   // fused CG direction update d = z + beta d_old
+          x = fma(a.sc[SC_BETA], a.dold[row], a.dz[row]);
+          if (blockIdx.x == 0) a.dnew[row] = x;
+        } else {
+          x = a.v[row];
+        }
+      }
+      vv[e] = (float)x;
+    }
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      if constexpr (PACK) {
+        vr[sl][j] = pack2(vv[2 * j], vv[2 * j + 1]);
+        yr[sl][j] = 0ull;
+      } else {
+        vr[sl][j] = vv[j];
+        yr[sl][j] = 0.f;
+      }
+    }
+  }
+  __syncthreads();   // barriers initialised before anyone waits on them
+
+  const int cl = lane % TC;
+  bool timed_out = false;
+  // stage of group i is i % S and its phase parity (i / S) & 1, both kept as running counters
+  int stage = 0, prev_stage = S - 1;
+  unsigned parity = 0;
+  int64_t col0 = (int64_t)blockIdx.x * TC;
+  for (int i = 0; i < my_groups; ++i, col0 += col_step) {
+    const TA* st = stages + (size_t)stage * stage_elems;
+    // after one wait has given up, the rest are skipped (and no further copies issued)
+    if (!timed_out && !mbar_wait_bounded(&bars[stage], parity)) timed_out = true;
+    const int ncols = (int)std::min<int64_t>(TC, a.n - col0);
+    const int64_t mycol = col0 + cl;
+    const bool cok = mycol < a.n;
+    const float w = cok ? a.d2f[mycol] : 0.f;
+    // column dots from the staged group; with KEEP the unpacked group stays in registers for
+    // the accumulation below instead of being read and unpacked a second time
+    Acc kept[KEEP ? TC : 1][KEEP ? SPW : 1][NA];
+    float pd[TC];
+#pragma unroll
+    for (int c = 0; c < TC; ++c) {
+      Acc acc{};
+      if (c < ncols) {
+#pragma unroll
+        for (int sl = 0; sl < SPW; ++sl) {
+          if (!rok[sl]) continue;
+          const uint4 r = *reinterpret_cast<const uint4*>(st + (size_t)c * a.lda + rowb[sl]);
+          Acc av[NA];
+          unpack_acc<TA, PACK>(r, av);
+#pragma unroll
+          for (int j = 0; j < NA; ++j) {
+            if constexpr (KEEP) kept[c][sl][j] = av[j];
+            if constexpr (PACK) acc = fma2(av[j], vr[sl][j], acc);
+            else acc = fmaf(av[j], vr[sl][j], acc);
+          }
+        }
+      }
+      if constexpr (PACK) pd[c] = sum2(acc);
+      else pd[c] = acc;
+    }
+    const float wsum = warp_transpose_reduce<TC, float>(pd, lane);
+    if (lane < TC) red[i & 1][warp][lane] = wsum;
+    __syncthreads();
+    // every warp is past group i-1: its stage may be refilled with group i + S - 1
+    if (threadIdx.x == 0 && !timed_out && i + S - 1 < my_groups) {
+      fence_proxy_async_smem();
+      issue(i + S - 1, prev_stage);
+    }
+    float dot = 0.f;
+    for (int wi = 0; wi < nwarps; ++wi) dot += red[i & 1][wi][cl];
+    const float cf = cok ? w * dot : 0.f;
+    if (a.colout && warp == 0 && lane < TC && cok) a.colout[mycol] = (double)dot;
+#pragma unroll
+    for (int c = 0; c < TC; ++c) {
+      const float cc = __shfl_sync(kFull, cf, c);
+      if (c >= ncols) continue;
+#pragma unroll
+      for (int sl = 0; sl < SPW; ++sl) {
+        if (!rok[sl]) continue;
+        Acc av[NA];
+        if constexpr (KEEP) {
+#pragma unroll
+          for (int j = 0; j < NA; ++j) av[j] = kept[c][sl][j];
+        } else {
+          const uint4 r = *reinterpret_cast<const uint4*>(st + (size_t)c * a.lda + rowb[sl]);
+          unpack_acc<TA, PACK>(r, av);
+        }
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          if constexpr (PACK) yr[sl][j] = fma2(pack2(cc, cc), av[j], yr[sl][j]);
+          else yr[sl][j] = fmaf(cc, av[j], yr[sl][j]);
+        }
+      }
+    }
+    prev_stage = stage;
+    if (++stage == S) {
+      stage = 0;
+      parity ^= 1u;
+    }
+  }
+  if (timed_out) s_timeout = 1;
+  __syncthreads();
+  if (s_timeout) {
+    if (threadIdx.x == 0) {
+      if (a.flw) a.flw[FL_TIMEOUT] = 1;
+      // let copies still in flight land before the CTA's shared memory goes away
+      for (int i = std::max(0, my_groups - S); i < my_groups; ++i)
+        mbar_wait_bounded(&bars[i % S], (unsigned)((i / S) & 1));
+    }
+    __syncthreads();
+  }
+
+  if (a.qacc) {
+    // kQCopies copies of q spread the atomic traffic over more L2 lines
+    float* qc = a.qacc + (size_t)(blockIdx.x % kQCopies) * a.m;
+#pragma unroll
+    for (int sl = 0; sl < SPW; ++sl)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const int row = rowb[sl] + e;
+        if (rok[sl] && row < a.m) atomicAdd(&qc[row], acc_elem<PACK>(yr[sl], e));
+      }
+    // last CTA: d^T q and alpha (no waiting: the last CTA to arrive does the work)
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(a.cnt, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double dq[1] = {0.0};
+    for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
+      float qi = 0.f;
+#pragma unroll
+      for (int k = 0; k < kQCopies; ++k) qi += __ldcg(&a.qacc[(size_t)k * a.m + i]);
+      dq[0] += a.dnew[i] * (double)qi;
+    }
+    block_sum<1>(dq);
+    if (threadIdx.x == 0) {
+      *a.cnt = 0u;
+      a.scw[SC_DQ] = dq[0];
+      if (!(dq[0] > 0.0) || !isfinite(dq[0])) {
+        a.flw[FL_NUMERIC] = 1;
+        a.flw[FL_DONE] = 1;
+        a.scw[SC_ALPHA] = 0.0;
+      } else {
+        a.scw[SC_ALPHA] = a.scw[SC_RHO] / dq[0];
+      }
+    }
+    return;
+  }
+  float* part = reinterpret_cast<float*>(a.part);
+#pragma unroll
+  for (int sl = 0; sl < SPW; ++sl)
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      const int row = rowb[sl] + e;
+      if (rok[sl] && row < a.m) part[(size_t)blockIdx.x * a.m + row] = acc_elem<PACK>(yr[sl], e);
+    }
+}
+
+namespace {
+
+constexpr size_t kSmemBudget = 200 * 1024;   // dynamic shared memory per SM used by the pass
+
+// Inner-loop variants: PACK (paired FP32 FMAs), KEEP (unpacked group kept in registers when a
+// warp has one row slice).  Measured on GB300 (m = 1000 and 2000, n = 200000 and 500000):
+// paired FMAs are slower for every type; keeping the group is 15-20% faster for 16-bit types
+// and slower for FP32, so the default keeps it for 16-bit types only; groups of 16 columns
+// were slower than groups of 8.  LP_CGPROD_PACK / LP_CGPROD_KEEP (0 or 1) override.
+#ifndef LP_CGPROD_PACK
+#define LP_CGPROD_PACK 0
+#endif
+constexpr bool kPack = LP_CGPROD_PACK != 0;
+template <typename TA>
+constexpr bool keep_default() {
+#ifdef LP_CGPROD_KEEP
+  return LP_CGPROD_KEEP != 0;
+#else
+  return sizeof(TA) == 2;
+#endif
+}
+
+template <typename TA, int SPW, int TC>
+int launch_cgprod_t(ColArgs a, int nwarps, int num_sms, int max_grid, cudaStream_t st) {
+  const size_t col_bytes = (size_t)a.lda * sizeof(TA);
+  const size_t stage = (size_t)TC * col_bytes;
+  // enough warps per SM to hide shared-memory latency: up to 4 CTAs of few warps
+  int ctas = std::max(1, std::min(4, 16 / nwarps));
+  int S = 0;
+  for (; ctas >= 1; --ctas) {
+    S = (int)std::min<size_t>(6, (kSmemBudget / ctas) / (stage + 8));
+    if (S >= 3) break;
+  }
+  if (ctas < 1) {
+    ctas = 1;
+    S = (int)std::min<size_t>(6, kSmemBudget / (stage + 8));
+  }
+  if (S < 2) return -1;
+  const size_t smem = (size_t)S * stage + (size_t)S * 8;
+  auto kern = k_cgprod<TA, SPW, TC, kPack, keep_default<TA>() && SPW == 1>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  const int64_t ngroups = (a.n + TC - 1) / TC;
+  int64_t grid = (int64_t)num_sms * ctas;
+  if (grid > max_grid) grid = max_grid;
+  if (grid > ngroups) grid = ngroups;
+  if (grid < 1) grid = 1;
+  { note_launch(); kern<<<(unsigned)grid, nwarps * 32, smem, st>>>(a, S, ngroups); }
+  return (int)grid;
+}
+
+template <typename TA>
+int launch_cgprod_dt(ColArgs a, int num_sms, int max_grid, cudaStream_t st) {
+  constexpr int VEC = VecN<TA>::N;
+  const int nslices = (a.m + 32 * VEC - 1) / (32 * VEC);
+  int spw = 1;
+  while ((nslices + spw - 1) / spw > 16) spw *= 2;
+  if (spw > 4) return -1;
+  const int nwarps = (nslices + spw - 1) / spw;
+  // groups of 8 columns while a stage stays within 64 KB, else of 2
+  const bool wide_cols = (size_t)8 * a.lda * sizeof(TA) > 64 * 1024;
+  switch (spw) {
+    case 1:
+      return wide_cols ? launch_cgprod_t<TA, 1, 2>(a, nwarps, num_sms, max_grid, st)
+                       : launch_cgprod_t<TA, 1, 8>(a, nwarps, num_sms, max_grid, st);
+    case 2:
+      return wide_cols ? launch_cgprod_t<TA, 2, 2>(a, nwarps, num_sms, max_grid, st)
+                       : launch_cgprod_t<TA, 2, 8>(a, nwarps, num_sms, max_grid, st);
+    default:
+      return wide_cols ? launch_cgprod_t<TA, 4, 2>(a, nwarps, num_sms, max_grid, st)
+                       : launch_cgprod_t<TA, 4, 8>(a, nwarps, num_sms, max_grid, st);
+  }
+}
+
+}  // namespace
+
+// Returns the number of CTAs (partial rows) or -1 when the shape is not covered (the caller
+// then uses the register-tiled pass).  Needs a.d2f (the FP32 weight).
+int launch_cgprod(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t st) {
+  if (!a.d2f) return -1;
+  switch (ta) {
+    case LP_F32: return launch_cgprod_dt<float>(a, num_sms, max_grid, st);
+    case LP_BF16: return launch_cgprod_dt<__nv_bfloat16>(a, num_sms, max_grid, st);
+    case LP_F16: return launch_cgprod_dt<__half>(a, num_sms, max_grid, st);
+    default: return -1;
+  }
+}
+
+}  // namespace lpk

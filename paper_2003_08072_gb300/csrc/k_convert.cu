@@ -85,6 +85,56 @@ cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, i
   return cudaErrorInvalidValue;
 }
 
+// Column-scaled low-precision copy: column j of the master matrix (column-major, leading dim
+// lda, m rows) is multiplied by 2^-e_j, with e_j chosen so that max_i |a_ij| 2^-e_j lies in
+// [0.5, 1), and rounded to TD; cs2[j] = 2^(2 e_j).  A power of two is exact in every format, so
+// A D^2 A^T = A_s (S^2 D^2) A_s^T with A_s the stored copy and S = diag(2^e_j): the scales move
+// into the FP32 weight of the product and the copy keeps the format's full relative precision
+// whatever the column norms (FP16 would otherwise overflow or go subnormal).  One warp per
+// column.
+template <typename TS, typename TD>
+__global__ void k_conv_colscaled(const TS* __restrict__ src, int lda, int m, int64_t n,
+                                 TD* __restrict__ dst, int ldd, float* __restrict__ cs2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t col = wid; col < n; col += nw) {
+    const TS* a = src + col * (int64_t)lda;
+    double mx = 0.0;
+    for (int r = lane; r < m; r += 32) mx = fmax(mx, fabs((double)a[r]));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) mx = fmax(mx, __shfl_xor_sync(kFull, mx, off));
+    int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
+    e = e < -60 ? -60 : (e > 60 ? 60 : e);
+    if (lane == 0) cs2[col] = ldexpf(1.0f, 2 * e);
+    TD* o = dst + col * (int64_t)ldd;
+    for (int r = lane; r < ldd; r += 32) o[r] = to_dt<TD>(r < m ? ldexp((double)a[r], -e) : 0.0);
+  }
+}
+
+template <typename TS, typename TD>
+static cudaError_t conv_scaled_t(const void* src, int lda, int m, int64_t n, void* dst, int ldd,
+                                 float* cs2, cudaStream_t st) {
+  int64_t g = (n * 32 + 255) / 256;
+  if (g > 8192) g = 8192;
+  { note_launch(); k_conv_colscaled<TS, TD><<<(unsigned)g, 256, 0, st>>>((const TS*)src, lda, m, n, (TD*)dst, ldd, cs2); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_colscaled(const void* src, lp_dtype sdt, int lda, int m, int64_t n,
+                                     void* dst, lp_dtype ddt, int ldd, float* cs2,
+                                     cudaStream_t st) {
+  if (sdt == LP_F32 && ddt == LP_BF16)
+    return conv_scaled_t<float, __nv_bfloat16>(src, lda, m, n, dst, ldd, cs2, st);
+  if (sdt == LP_F32 && ddt == LP_F16)
+    return conv_scaled_t<float, __half>(src, lda, m, n, dst, ldd, cs2, st);
+  if (sdt == LP_F64 && ddt == LP_BF16)
+    return conv_scaled_t<double, __nv_bfloat16>(src, lda, m, n, dst, ldd, cs2, st);
+  if (sdt == LP_F64 && ddt == LP_F16)
+    return conv_scaled_t<double, __half>(src, lda, m, n, dst, ldd, cs2, st);
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 __global__ void k_check_finite(const T* src, int64_t count, int* flag) {
   int bad = 0;

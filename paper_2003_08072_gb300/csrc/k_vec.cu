@@ -89,7 +89,7 @@ cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st) {
 __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ s, int64_t n,
                        double* __restrict__ d2, double* __restrict__ d, double* sc, double* bpart,
                        unsigned* bcnt, double sigma, const double* __restrict__ c,
-                       float* __restrict__ d2f) {
+                       float* __restrict__ d2f, const float* __restrict__ cs2) {
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -97,7 +97,7 @@ __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ 
     const double q = xi / si;
     d2[i] = q;
     d[i] = sqrt(q);
-    if (d2f) d2f[i] = (float)q;
+    if (d2f) d2f[i] = (float)(cs2 ? q * (double)cs2[i] : q);
     v[0] += xi * si;
     v[1] += c[i] * xi;
   }
@@ -118,8 +118,21 @@ static int vec_grid(int64_t n) {
 
 cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
                                 double* sc, double* bpart, unsigned* bcnt, double sigma,
-                                const double* c, cudaStream_t st, float* d2f) {
-  { note_launch(); k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c, d2f); }
+                                const double* c, cudaStream_t st, float* d2f, const float* cs2) {
+  { note_launch(); k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c, d2f, cs2); }
+  return cudaGetLastError();
+}
+
+// FP32 weight of the streamed product: d2f = d2 (times the copy's column scales cs2, if any).
+__global__ void k_d2f(const double* __restrict__ d2, const float* __restrict__ cs2, int64_t n,
+                      float* __restrict__ d2f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d2f[i] = (float)(cs2 ? d2[i] * (double)cs2[i] : d2[i]);
+}
+
+cudaError_t launch_d2f(const double* d2, const float* cs2, int64_t n, float* d2f, cudaStream_t st) {
+  { note_launch(); k_d2f<<<vec_grid(n), 256, 0, st>>>(d2, cs2, n, d2f); }
   return cudaGetLastError();
 }
 

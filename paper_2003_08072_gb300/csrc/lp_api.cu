@@ -116,9 +116,10 @@ static void dfree(void* p) {
 extern "C" void lp_destroy(lp_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
-  if (c->own_As) dfree(c->As);
+  if (c->own_As) dfree(c->As_req);
   dfree(c->A);
-  if (c->own_svals) dfree(c->svals);
+  dfree(c->cs2);
+  if (c->own_svals) dfree(c->svals_req);
   dfree(c->colptr);
   dfree(c->rowidx);
   dfree(c->vals);
@@ -230,6 +231,17 @@ static void prof_harvest(lp_ctx* c) {
 
 // Harvests the CG product events of one batch: the first `real` launches did work, the rest
 // found the CG finished and returned at once.
+// Algorithmic bytes of one CG product on the copy streamed now: A once, D^2 (FP32 weight or
+// FP64), the direction in and the product out (CSC: values, row ids and column pointers).
+static double matvec_bytes(const lp_ctx* c) {
+  const double wb = c->s_dtype == LP_F64 ? 8.0 : 4.0;
+  if (!c->sparse)
+    return (double)c->m * (double)c->n * (double)dtype_size(c->s_dtype) + wb * (double)c->n +
+           16.0 * c->m;
+  return (double)c->nnz * (dtype_size(c->s_dtype) + 4.0) + 8.0 * (c->n + 1) + 8.0 * (double)c->n +
+         16.0 * c->m;
+}
+
 static void prof_harvest_mv(lp_ctx* c, int real) {
   for (size_t i = 0; i < c->mv_pending.size(); ++i) {
     auto& pr = c->mv_pending[i];
@@ -237,6 +249,7 @@ static void prof_harvest_mv(lp_ctx* c, int real) {
     if ((int)i < real && pr.a && pr.b && cudaEventElapsedTime(&ms, pr.a, pr.b) == cudaSuccess) {
       c->prof.matvec_ms += ms;
       c->prof.matvec_count += 1;
+      c->mv_bytes_sum += matvec_bytes(c);
     }
     cudaGetLastError();
     ev_put(c, pr.a);
@@ -265,6 +278,8 @@ static lp_status sync_scalars(lp_ctx* c) {
   LP_CU(cudaMemcpyAsync(c->fl_h, c->fl, FL_COUNT * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   LP_CU(cudaStreamSynchronize(c->st));
   if (!c->ev_pending.empty()) prof_harvest(c);
+  if (c->fl_h[FL_TIMEOUT])
+    return fail(LP_ERR_TIMEOUT, "a bounded wait for a bulk copy of A gave up");
   return LP_OK;
 }
 
@@ -356,9 +371,17 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
       if ((st = dalloc((unsigned char**)&c->As, (size_t)c->lda_s * n * dtype_size(sd))) != LP_OK)
         return bail(st);
       c->own_As = true;
-      // convert from the master copy (column-major with leading dim lda): walk as an
-      // lda x n matrix, padding rows are zero already.
-      e = launch_convert_dense(c->A, a_dtype, false, c->lda, n, c->As, sd, c->lda_s, c->st);
+      if (sd == LP_BF16 || sd == LP_F16) {
+        // 16-bit copies are stored column-scaled by powers of two (scales folded into D^2)
+        if ((st = dalloc(&c->cs2, (size_t)n)) != LP_OK) return bail(st);
+        e = launch_convert_colscaled(c->A, a_dtype, c->lda, m, n, c->As, sd, c->lda_s, c->cs2,
+                                     c->st);
+        c->cs2_on = true;
+      } else {
+        // convert from the master copy (column-major with leading dim lda): walk as an
+        // lda x n matrix, padding rows are zero already.
+        e = launch_convert_dense(c->A, a_dtype, false, c->lda, n, c->As, sd, c->lda_s, c->st);
+      }
       if (e != cudaSuccess) return bail(lp_cuda_fail(e, "stream copy"));
     }
   } else {
@@ -407,6 +430,10 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
       c->s_dtype = LP_F32;
     }
   }
+  c->s_dtype_req = c->s_dtype;
+  c->As_req = c->As;
+  c->lda_s_req = c->lda_s;
+  c->svals_req = c->svals;
   // norms of b and c for the stopping rule
   LP_CU(launch_norm2(c->b, m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
   if ((st = sync_scalars(c)) != LP_OK) return bail(st);
@@ -441,7 +468,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
                              int red_mode, double* out, const double* p0, int skip_if_done,
                              bool record_mv = false, const double* dz = nullptr,
                              const double* dold = nullptr, double* dnew = nullptr,
-                             float* qacc = nullptr) {
+                             float* qacc = nullptr, bool weight_in_d2f = false) {
   int nblk;
   bool acc64;
   cudaEvent_t ea = nullptr, eb = nullptr;
@@ -455,7 +482,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     a.n = c->n;
     a.v = v;
     a.d2 = w;
-    a.d2f = (!precise && w == c->d2) ? c->d2f : nullptr;
+    a.d2f = (!precise && (w == c->d2 || weight_in_d2f)) ? c->d2f : nullptr;
     a.colout = t;
     a.part = c->part;
     a.fl = c->fl;
@@ -465,15 +492,18 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     a.dold = dold;
     a.dnew = dnew;
     acc64 = precise || ta == LP_F64;
+    a.flw = c->fl;
     if (qacc && !acc64) {
       a.qacc = qacc;
       a.cnt = c->bcnt + 1;
       a.scw = c->sc;
-      a.flw = c->fl;
     } else {
       qacc = nullptr;
     }
-    nblk = launch_coltile(ta, acc64, MODE_NORMAL, a, c->num_sms, c->st);
+    nblk = -1;
+    if (!acc64 && a.d2f && c->use_staged)
+      nblk = launch_cgprod(ta, a, c->num_sms, coltile_max_grid(c->num_sms), c->st);
+    if (nblk < 0) nblk = launch_coltile(ta, acc64, MODE_NORMAL, a, c->num_sms, c->st);
   } else {
     CscArgs a{};
     const lp_dtype tv = precise ? c->a_dtype : c->s_dtype;
@@ -563,12 +593,40 @@ static lp_status pass_gram(lp_ctx* c, const double* G, const double* v, double* 
   return LP_OK;
 }
 
+// Column scales of the streamed copy in use (NULL when it is unscaled).
+static const float* stream_cs2(const lp_ctx* c) { return c->cs2_on ? c->cs2 : nullptr; }
+
+// Every solve starts on the stream copy asked for at lp_create.
+static void stream_reset(lp_ctx* c) {
+  launch_set(nullptr, 0, 0.0, c->fl, FL_TIMEOUT, 0, c->st);
+  c->s_dtype = c->s_dtype_req;
+  c->As = c->As_req;
+  c->lda_s = c->lda_s_req;
+  c->svals = c->svals_req;
+  c->cs2_on = c->cs2 != nullptr;
+  c->switch_iter = -1;
+}
+
+// Stream the master copy instead (FP32 for an FP32 input, FP64 for an FP64 one) for the rest
+// of the solve; the FP32 weight of the product is recomputed without the copy's scales.
+// Returns false when the master copy is already the one streamed.
+static bool stream_switch(lp_ctx* c, int k) {
+  if (c->s_dtype == c->a_dtype) return false;
+  c->s_dtype = c->a_dtype;
+  c->As = c->A;
+  c->lda_s = c->lda;
+  c->svals = c->vals;
+  c->cs2_on = false;
+  c->switch_iter = k;
+  return launch_d2f(c->d2, nullptr, c->n, c->d2f, c->st) == cudaSuccess;
+}
+
 // Alg. 2 step (b): d2, d, mu from (x, s); r_p, r_d, p in one pass; ||r_p||^2, ||r_d||^2.
 static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, const double* s,
                                double sigma, double* rp, double* rd, double* p) {
   PhaseScope ps(c, LP_PH_RESIDUALS);
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, sigma, c->c, c->st,
-                            c->d2f));
+                            c->d2f, stream_cs2(c)));
   int nblk;
   if (!c->sparse) {
     ColArgs a{};
@@ -742,9 +800,9 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
   double abs_thr = INFINITY;
   if (c->prm.cg_theory_rule)
     abs_thr = c->prm.gamma * c->prm.sigma * sqrt(mu) / (4.0 * sqrt((double)c->n));
-  const bool lowprec = c->s_dtype != LP_F64;   // CG products accumulate in FP32
-  double rho0 = 0.0, target2 = 0.0;
-  int total_it = 0, outer = 0;
+  bool lowprec = c->s_dtype != LP_F64;   // CG products accumulate in FP32
+  double rho0 = 0.0, target2 = 0.0, f2_prev = INFINITY, contraction = 0.0;
+  int total_it = 0, outer = 0, rounds = 0;
   for (;;) {
     int it = 0;
     double r0 = 0.0, rl = 0.0;
@@ -756,11 +814,13 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
                          isfinite(abs_thr) ? abs_thr * abs_thr : INFINITY);
     } else {
       // refinement: solve (A D^2 A^T) delta = -r~ and add it to dy.  The residual of
-      // dy + delta is the residual of this solve, so it stops at the solve's own target
-      // (relative rule off: a relative 1e-6 of the already small residual would over-solve).
+      // dy + delta is the residual of this solve, so it stops at the solve's own target, or
+      // once its own residual is below what the streamed operator can deliver in one round
+      // (the contraction of the previous round times the current ||f||): solving the
+      // rounded system further would not shrink the true residual.
       LP_CU(launch_vec_ops(VOP_NEG, c->rhs, c->rtil, nullptr, m, nullptr, c->st));
-      LP_TRY(run_pcg(c, 0, c->rhs, c->dy, INFINITY, 0.5 * sqrt(target2), c->prm.cg_max_iter,
-                     &it, &r0, &rl));
+      const double thr = std::max(0.5 * sqrt(target2), 0.5 * contraction * sqrt(f2_prev));
+      LP_TRY(run_pcg(c, 0, c->rhs, c->dy, INFINITY, thr, c->prm.cg_max_iter, &it, &r0, &rl));
       LP_CU(launch_vec_ops(VOP_ADD, c->dyacc, c->dyacc, c->dy, m, nullptr, c->st));
     }
     total_it += it;
@@ -777,8 +837,28 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
     if (!isfinite(f2)) return fail(LP_ERR_NUMERIC, "non-finite residual in the normal solve");
     so->f_norm = sqrt(std::max(f2, 0.0));
     so->f_target = sqrt(target2);
-    if (!lowprec || f2 <= 4.0 * target2 || outer >= c->prm.refine_max) break;
+    if (!lowprec || f2 <= 4.0 * target2) break;
+    // Refinement converges when the streamed operator is close enough to A D^2 A^T in the
+    // preconditioned norm; rounding A to 16 bits perturbs it by ~2^-9 relative per entry,
+    // which a badly conditioned A D stretches past 1.  A round that fails to halve ||f||
+    // (or the round cap) switches the solve to the master copy for the remaining IPM
+    // iterations; without a copy to switch to, the cap ends the refinement.
+    // contraction of this round: ||f|| after it over ||f|| before it (round 0 starts from
+    // ||f^(0)|| = sqrt(rho0)); 1/8 or worse after the first solve also means many rounds
+    contraction = sqrt(f2 / (rounds == 0 ? std::max(rho0, 1e-300) : f2_prev));
+    const bool stalled = (rounds == 0 && contraction > 0.125) || (rounds >= 1 && f2 > 0.25 * f2_prev);
+    if (stalled || rounds >= c->prm.refine_max) {
+      if (!stream_switch(c, k)) {
+        if (rounds >= c->prm.refine_max) break;
+      } else {
+        lowprec = c->s_dtype != LP_F64;
+        rounds = 0;
+        contraction = 0.0;   // the master copy's rounds solve to the target
+      }
+    }
+    f2_prev = f2;
     ++outer;
+    ++rounds;
   }
   so->cg_iters = total_it;
   // u = (A D W)^dagger r~ = (A D W)^T q with Q q = r~ (Eq. compv, full row rank): PCG on
@@ -816,6 +896,7 @@ static lp_status run_step(lp_ctx* c, double* x, double* y, double* s, const doub
 extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, int32_t start_given,
                                   lp_info* info) {
   if (!c || !x || !y || !s) return fail(LP_ERR_ARG, "lp_ipm_solve: NULL argument");
+  stream_reset(c);
   const int m = c->m;
   const int64_t n = c->n;
   lp_info inf{};
@@ -888,6 +969,8 @@ extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, in
   }
   inf.ipm_iters = k;
   inf.status = result;
+  inf.stream_dtype = c->s_dtype;
+  inf.stream_switch_iter = c->switch_iter;
   LP_CU(cudaMemcpyAsync(x, c->x, n * sizeof(double), cudaMemcpyDefault, c->st));
   LP_CU(cudaMemcpyAsync(y, c->y, m * sizeof(double), cudaMemcpyDefault, c->st));
   LP_CU(cudaMemcpyAsync(s, c->s, n * sizeof(double), cudaMemcpyDefault, c->st));
@@ -901,8 +984,9 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
                                      double* Atdy, lp_info* info) {
   if (!c || !x || !s || !p || !dy) return fail(LP_ERR_ARG, "lp_normal_solve: NULL argument");
   if (k < 0) return fail(LP_ERR_ARG, "lp_normal_solve: k < 0");
+  stream_reset(c);
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
-                            c->c, c->st, c->d2f));
+                            c->c, c->st, c->d2f, stream_cs2(c)));
   LP_TRY(sync_scalars(c));
   const double mu = c->sc_h[SC_MU];
   if (!(mu > 0) || !isfinite(mu)) return fail(LP_ERR_ARG, "lp_normal_solve: x, s must be positive");
@@ -925,6 +1009,8 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
     inf.f_norm = so.f_norm;
     inf.f_target = so.f_target;
     inf.mu = mu;
+    inf.stream_dtype = c->s_dtype;
+    inf.stream_switch_iter = c->switch_iter;
     *info = inf;
   }
   return LP_OK;
@@ -979,6 +1065,7 @@ extern "C" lp_status lp_normal_matvec(lp_ctx* c, const double* d2, const double*
                                       double* t, lp_dtype stream_dtype) {
   if (!c || !d2 || !v || !y) return fail(LP_ERR_ARG, "lp_normal_matvec: NULL argument");
   bool precise;
+  stream_reset(c);
   if (stream_dtype == LP_F64) {
     precise = true;
   } else if (stream_dtype == c->s_dtype) {
@@ -986,7 +1073,12 @@ extern "C" lp_status lp_normal_matvec(lp_ctx* c, const double* d2, const double*
   } else {
     return fail(LP_ERR_ARG, "lp_normal_matvec: stream dtype differs from the context's");
   }
-  LP_TRY(pass_normal(c, precise, v, d2, t, RED_PLAIN, y, nullptr, 0));
+  if (!precise && c->s_dtype != LP_F64) {
+    // the FP32-accumulated product takes its weight as FP32 (with the copy's column scales)
+    LP_CU(launch_d2f(d2, stream_cs2(c), c->n, c->d2f, c->st));
+  }
+  LP_TRY(pass_normal(c, precise, v, d2, t, RED_PLAIN, y, nullptr, 0, false, nullptr, nullptr,
+                     nullptr, nullptr, !precise && c->s_dtype != LP_F64));
   LP_CU(cudaStreamSynchronize(c->st));
   return LP_OK;
 }
@@ -997,7 +1089,7 @@ extern "C" lp_status lp_step(lp_ctx* c, double* x, double* y, double* s, const d
   if (!c || !x || !y || !s || !rd || !dy || !Atdy || !Wu) return fail(LP_ERR_ARG, "lp_step: NULL argument");
   if (!(mu0 > 0)) return fail(LP_ERR_ARG, "lp_step: mu0 must be positive");
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
-                            c->c, c->st, c->d2f));
+                            c->c, c->st, c->d2f, stream_cs2(c)));
   (void)mu;  // mu is recomputed from x and s on the device
   LP_TRY(run_step(c, x, y, s, rd, dy, Atdy, Wu, eta, mu0, dx ? dx : c->dx, ds ? ds : c->ds));
   LP_TRY(sync_scalars(c));
@@ -1020,19 +1112,14 @@ extern "C" lp_status lp_profile_read(lp_ctx* c, lp_profile* out, int32_t reset) 
   if (!c || !out) return fail(LP_ERR_ARG, "lp_profile_read: NULL");
   LP_CU(cudaStreamSynchronize(c->st));
   if (!c->ev_pending.empty()) prof_harvest(c);
-  if (!c->sparse) {
-    c->prof.matvec_bytes = (double)c->m * (double)c->n * (double)dtype_size(c->s_dtype) +
-                           8.0 * (double)c->n + 8.0 * c->m;
-  } else {
-    c->prof.matvec_bytes = (double)c->nnz * (dtype_size(c->s_dtype) + 4.0) + 8.0 * (c->n + 1) +
-                           8.0 * (double)c->n + 8.0 * c->m;
-  }
+  // average over the timed products (the streamed copy may change within a solve)
+  c->prof.matvec_bytes = c->prof.matvec_count > 0 ? c->mv_bytes_sum / c->prof.matvec_count
+                                                  : matvec_bytes(c);
   c->prof.launches = g_launches.load();
   *out = c->prof;
   if (reset) {
-    lp_profile z{};
-    z.matvec_bytes = c->prof.matvec_bytes;
-    c->prof = z;
+    c->prof = lp_profile{};
+    c->mv_bytes_sum = 0.0;
   }
   return LP_OK;
 }

@@ -48,6 +48,7 @@ enum Flag {
   FL_NUMERIC,    // non-finite or non-positive curvature seen
   FL_BREAK,      // non-positive pivot in the factorization
   FL_MAXIT,      // CG iteration cap of the current solve
+  FL_TIMEOUT,    // a bounded wait in a kernel gave up
   FL_COUNT = 8
 };
 
@@ -77,6 +78,17 @@ struct lp_ctx {
   void* As = nullptr;          // == A when s_dtype == a_dtype
   int lda_s = 0;
   bool own_As = false;
+  float* cs2 = nullptr;        // BF16/F16 copy: per-column 2^(2 e_j) (the copy holds A_j 2^-e_j)
+  bool cs2_on = false;         // the streamed copy in use is the scaled one
+  // the stream copy asked for at lp_create; a solve whose FP64 refinement stops contracting
+  // switches to streaming the master copy (s_dtype = a_dtype) until the next solve starts
+  lp_dtype s_dtype_req = LP_F64;
+  void* As_req = nullptr;
+  int lda_s_req = 0;
+  void* svals_req = nullptr;
+  int switch_iter = -1;        // IPM iteration of the last switch (-1: none)
+  bool use_staged = true;      // CG products through the shared-memory staged pass
+  double mv_bytes_sum = 0.0;   // algorithmic bytes of the timed CG products
 
   // CSC (sparse) copy: column pointers, row ids, values
   int64_t nnz = 0;
@@ -200,6 +212,9 @@ struct ColArgs {
 // Dense column-tile pass.  acc_f64 selects FP64 accumulation (else FP32).
 // Returns the number of CTAs used (partials rows), or -1 on an unsupported shape.
 int launch_coltile(lp_dtype ta, bool acc_f64, int mode, ColArgs a, int num_sms, cudaStream_t st);
+// CG product (MODE_NORMAL, FP32 accumulation, FP32 weight a.d2f) with A staged through shared
+// memory by bulk copies (k_cgprod.cu); -1 when the shape or dtype is not covered.
+int launch_cgprod(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t st);
 
 // Sparse (CSC) passes
 struct CscArgs {
@@ -248,7 +263,9 @@ cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st);
 // n-vector kernels
 cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
                                 double* sc, double* bpart, unsigned* bcnt, double sigma,
-                                const double* c, cudaStream_t st, float* d2f = nullptr);
+                                const double* c, cudaStream_t st, float* d2f = nullptr,
+                                const float* cs2 = nullptr);
+cudaError_t launch_d2f(const double* d2, const float* cs2, int64_t n, float* d2f, cudaStream_t st);
 cudaError_t launch_norm2(const double* v, int64_t n, double* sc, int slot, double* bpart,
                          unsigned* bcnt, cudaStream_t st);
 
@@ -333,6 +350,9 @@ int gram_split(int m, int w, int num_sms);
 // conversions
 cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, int m, int64_t n,
                                  void* dst, lp_dtype ddt, int ldd, cudaStream_t st);
+cudaError_t launch_convert_colscaled(const void* src, lp_dtype sdt, int lda, int m, int64_t n,
+                                     void* dst, lp_dtype ddt, int ldd, float* cs2,
+                                     cudaStream_t st);
 cudaError_t launch_check_finite(const void* src, lp_dtype dt, int64_t count, int* flag,
                                 cudaStream_t st);
 

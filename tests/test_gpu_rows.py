@@ -184,12 +184,14 @@ def test_normal_matvec_fp64(case):
 
 
 @pytest.mark.parametrize("sd", ["f32", "bf16", "f16"])
-def test_normal_matvec_low_precision_stream(sd):
+@pytest.mark.parametrize("m,n", [(300, 20_011), (2000, 6007), (5001, 5003), (8192, 8209)])
+def test_normal_matvec_low_precision_stream(sd, m, n):
     """FP32 accumulation over A streamed in the given precision, against the exactly rounded
-    matrix in FP64: relative error within 64 u_fp32 sqrt(m) of the |A| D^2 |A|^T |v| scale."""
+    matrix in FP64: relative error within 64 u_fp32 sqrt(m) of the |A| D^2 |A|^T |v| scale.
+    The sizes span the shapes of the staged product: 1 to 4 row slices per warp, column
+    groups of 8 and of 2, a ragged last group, the largest m."""
     import paper_2003_08072_gb300 as pkg
 
-    m, n = 300, 20_011
     code = pkg.DTYPE_CODES[sd]
     solver, A, lp, prm = make("dense", m, n, "f64", stream_dtype=code)
     x, y, sv = synth.iterate_point(9, m, n, spread=2.0)
