@@ -42,9 +42,18 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["dense", "sparse", "scaled"], default="dense",
+    ap.add_argument("--workload", choices=["dense", "sparse", "scaled", "serving"],
+                    default="dense",
                     help="dense: Gaussian m x n; sparse: CSR with --nnz-per-col nonzeros per "
-                         "column; scaled: dense with column scales 10^U(-3,3)")
+                         "column; scaled: dense with column scales 10^U(-3,3); serving: a "
+                         "Poisson stream of mixed dense/CSR LPs through the serving loop")
+    ap.add_argument("--requests", type=int, default=256, help="serving: stream length")
+    ap.add_argument("--rate", type=str, default="2000",
+                    help="serving: arrival rates in LP/s (comma separated, one run each)")
+    ap.add_argument("--max-live", type=int, default=16, help="serving: concurrent instances")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: admission budget")
+    ap.add_argument("--plain-sample", type=int, default=32,
+                    help="serving: requests solved one at a time on the plain FP64 path")
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--nnz-per-col", type=int, default=8)
@@ -57,7 +66,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-n", type=int, default=20_000)
     ap.add_argument("--cpu-sample-iters", type=int, default=4)
     args = ap.parse_args()
-    defaults = {"dense": (1000, 200_000), "sparse": (5000, 2_000_000), "scaled": (2000, 500_000)}
+    defaults = {"dense": (1000, 200_000), "sparse": (5000, 2_000_000), "scaled": (2000, 500_000),
+                "serving": (512, 102_400)}
     dm, dn = defaults[args.workload]
     args.m = args.m or dm
     args.n = args.n or dn
@@ -411,6 +421,167 @@ def run_ours(args, rank, world, local):
     return line
 
 
+# --------------------------------------------------------------------------- serving
+
+def _make_request(req):
+    import synth
+
+    kind, m, n, seed = req
+    return kind, synth.serving_instance(kind, m, n, seed)
+
+
+def serving_instances(count):
+    """The request stream: (kind, m, n, seed) from synth.serving_requests and its instances,
+    generated in a spawned process pool (before any CUDA use of the pool's workers)."""
+    import multiprocessing as mp
+
+    import synth
+
+    reqs = synth.serving_requests(count)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        return reqs, pool.map(_make_request, reqs, chunksize=1)
+
+
+def _submit(srv, pkg, kind, lp):
+    if kind == "dense":
+        return srv.submit(lp.m, lp.n, pkg.LP_DENSE_COLMAJOR, lp.At, lp.b, lp.c)
+    return srv.submit(lp.m, lp.n, pkg.LP_CSR, lp.values, lp.b, lp.c, indptr=lp.indptr,
+                      indices=lp.indices)
+
+
+def plain_fp64(pkg, insts, k):
+    """The first k requests one at a time on the plain path: A in FP64, FP64 stream, one
+    context per request, host buffers; returns (LP/s, objectives, seconds)."""
+    import numpy as np
+
+    prm = pkg.lp_params_default()
+    data = []
+    for kind, lp in insts[:k]:
+        if kind == "dense":
+            data.append((kind, lp, np.ascontiguousarray(lp.At, dtype=np.float64)))
+        else:
+            data.append((kind, lp, lp.values.astype(np.float64)))
+    objs = []
+    t0 = time.perf_counter()
+    for kind, lp, vals in data:
+        x, y, s = np.empty(lp.n), np.empty(lp.m), np.empty(lp.n)
+        if kind == "dense":
+            ctx = pkg.lp_create(lp.m, lp.n, pkg.LP_DENSE_COLMAJOR, pkg.LP_F64, vals, None, None,
+                                0, lp.b, lp.c, prm, None)
+        else:
+            ctx = pkg.lp_create(lp.m, lp.n, pkg.LP_CSR, pkg.LP_F64, vals, lp.indptr, lp.indices,
+                                lp.nnz, lp.b, lp.c, prm, None)
+        pkg.lp_ipm_solve(ctx, x, y, s)
+        pkg.lp_destroy(ctx)
+        objs.append(float(lp.c @ x))
+    secs = time.perf_counter() - t0
+    return k / secs, objs, secs
+
+
+def run_serving(args, rank, world, local):
+    import numpy as np
+
+    reqs, insts = serving_instances(args.requests)
+    import torch
+
+    import paper_2003_08072_gb300 as pkg
+
+    pkg.load(build_if_missing=False)
+    torch.cuda.set_device(local)
+    mine = [i for i in range(len(insts)) if i % world == rank]
+    prm = pkg.lp_params_default()
+    prm.stream_dtype = pkg.LP_BF16
+    runs = []
+    objs_batched, kkt_of = {}, {}
+    for rate in [float(r) for r in args.rate.split(",")]:
+        import synth
+
+        arrivals = synth.poisson_arrivals(len(insts), rate)
+        srv = pkg.LPServer(int(args.budget_gb * 2**30), max_live=args.max_live, params=prm)
+        # warm-up: one request of each kind, untimed
+        for i in range(2):
+            t = _submit(srv, pkg, *insts[i])
+            while srv.wait_any(60_000) != t:
+                pass
+            srv.result(t)
+        clk = ClockSampler(local)
+        clk.start()
+        barrier(world)
+        results = {}
+        done = threading.Event()
+
+        def collect():
+            while len(results) < len(mine):
+                t = srv.wait_any(1000)
+                if t is not None:
+                    results[t] = srv.result(t)
+            done.set()
+
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        tickets = {}
+        for i in mine:
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[_submit(srv, pkg, *insts[i])] = i
+        done.wait()
+        elapsed = max_over_ranks(time.perf_counter() - t0, world)
+        clocks = clk.stop()
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([r["latency_s"] for r in results.values()]) * 1e3
+        qd = np.array([r["queued_s"] for r in results.values()]) * 1e3
+        bad = [(insts[tickets[t]][0], insts[tickets[t]][1].m, insts[tickets[t]][1].n,
+                r["status"], r["error"]) for t, r in results.items() if r["status"] != 0]
+        for t, r in results.items():
+            i = tickets[t]
+            objs_batched[i] = float(insts[i][1].c @ r["x"])
+            if r["status"] == 0:
+                kkt_of[i] = max(r["info"].rp_rel, r["info"].rd_rel, r["info"].gap_rel)
+        runs.append({"rate": rate, "value": world * len(mine) / elapsed, "seconds": elapsed,
+                     "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                    "p99": float(np.percentile(lat, 99)),
+                                    "mean": float(lat.mean())},
+                     "queued_ms": {"p50": float(np.percentile(qd, 50)),
+                                   "p99": float(np.percentile(qd, 99))},
+                     "failed": len(bad), "failures": bad[:4], "peak_live": stats["peak_live"],
+                     "mem_peak_gb": stats["mem_peak"] / 2**30, "clocks": clocks})
+    if rank != 0:
+        return None
+    k = min(args.plain_sample, len(insts))
+    plain_v, plain_objs, plain_s = plain_fp64(pkg, insts, k)
+    rel = [abs(objs_batched[i] - plain_objs[i]) / abs(plain_objs[i]) for i in range(k)
+           if i in objs_batched]
+    # every request of the stream solved to the tolerance: scaled KKT of the returned iterate
+    kkt_max = max(kkt_of.values()) if kkt_of else None
+    best = runs[-1]
+    dense_elems = [m * n for kind, m, n, _ in reqs if kind == "dense"]
+    return {
+        "metric": "serving LPs/s (mixed dense FP32 / CSR 1% LP stream, Poisson arrivals)",
+        "value": best["value"], "unit": "LP/s", "n_gpus": world, "steps": len(insts),
+        "warmup": 2, "ms_per_step": 1e3 * best["seconds"] / len(insts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"{len(insts)} requests, m ~ U{{16..512}}, n = m U{{20..200}}, "
+                               "even requests dense Gaussian FP32, odd CSR at 1% density, "
+                               "Algorithm 2 to scaled KKT 1e-8 each",
+                   "mean_dense_elements": float(np.mean(dense_elems)),
+                   "max_live": args.max_live, "budget_gb": args.budget_gb,
+                   "stream_dtype": "bf16 (dense), f32 (CSR values)",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": best["latency_ms"], "queued_ms": best["queued_ms"],
+        "runs": runs,
+        "plain_fp64": {"value": plain_v, "unit": "LP/s", "sample": f"first {k} requests one at "
+                       "a time (FP64 A, FP64 stream, host buffers)", "seconds": plain_s},
+        "speedup_vs_plain_fp64": best["value"] / plain_v,
+        "max_rel_objective_diff_vs_plain": max(rel) if rel else None,
+        "max_scaled_kkt": kkt_max,
+        "clocks": best["clocks"],
+    }
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def oracle_iters_per_lp(args) -> float:
@@ -466,6 +637,8 @@ def main():
     rank, world, local = dist_setup()
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload == "serving":
+        line = run_serving(args, rank, world, local)
     else:
         line = run_ours(args, rank, world, local)
     if rank == 0 and line is not None:

@@ -297,6 +297,61 @@ lp_status lp_profile_enable(lp_ctx* ctx, int32_t on);
 /* lp_profile_read -- copies the accumulated profile into *out (host); reset != 0 zeroes it. */
 lp_status lp_profile_read(lp_ctx* ctx, lp_profile* out, int32_t reset);
 
+/* ---------------- memory footprint and the serving loop ---------------- */
+
+/*
+ * lp_footprint_bytes -- upper bound on the device bytes lp_create allocates for an instance of
+ * this shape (matrix copies, sketch, factor, workspaces), for admission control.  Pure host
+ * computation (no device call); num_sms <= 0 means 152.  Returns 0 for invalid sizes.
+ */
+uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, lp_dtype a_dtype, int64_t nnz,
+                            const lp_params* prm, int32_t num_sms);
+
+/*
+ * Serving: LP instances submitted one by one are solved with continuous batching.  max_live
+ * worker threads each own a CUDA stream; a free worker admits the oldest queued request as soon
+ * as its lp_footprint_bytes fits into the part of mem_budget_bytes not held by live requests,
+ * solves it with lp_create + lp_ipm_solve (Algorithm 2, parameters prm) and releases the memory.
+ * Live instances run concurrently on the GPU.  Admission is first come, first served.
+ * All buffers passed to the server are HOST memory; submit copies them, so the caller may
+ * reuse its buffers as soon as lp_server_submit returns.  One server per device; the device is
+ * the calling thread's current one at creation.  A server may be used from several threads.
+ */
+typedef struct lp_server lp_server;
+
+typedef struct {
+  int64_t submitted, completed, failed;   /* counts since creation (failed: status != LP_OK) */
+  int64_t queued, live, peak_live;        /* waiting, being solved, most solved at once */
+  uint64_t mem_in_use, mem_peak, mem_budget;  /* admitted footprints (bytes) */
+} lp_server_stats_t;
+
+/* Errors: LP_ERR_ARG (max_live outside 1..256, zero budget), LP_ERR_CUDA (no device). */
+lp_status lp_server_create(lp_server** out, uint64_t mem_budget_bytes, int32_t max_live,
+                           const lp_params* prm);
+
+/* Queues one instance (arguments as lp_create, host memory only); *ticket identifies it.
+ * Errors: LP_ERR_ARG, LP_ERR_OOM (the instance alone exceeds the budget). */
+lp_status lp_server_submit(lp_server* srv, int32_t m, int64_t n, lp_layout layout,
+                           lp_dtype a_dtype, const void* A_vals, const int64_t* indptr,
+                           const int32_t* indices, int64_t nnz, const double* b, const double* c,
+                           int64_t* ticket);
+
+/* Waits up to timeout_ms for a finished request not yet handed out and returns its ticket
+ * (completion order).  LP_ERR_TIMEOUT if none finished in time. */
+lp_status lp_server_wait_any(lp_server* srv, int32_t timeout_ms, int64_t* ticket);
+
+/* Result of a finished request: x, y, s (host, n / m / n float64, each may be NULL), the
+ * lp_info of its solve, and times[3] (may be NULL) = seconds queued, seconds being solved,
+ * latency from submission to completion.  Releases the ticket.  Returns the solve's status
+ * (its message in lp_last_error), or LP_ERR_ARG for an unknown or unfinished ticket. */
+lp_status lp_server_result(lp_server* srv, int64_t ticket, double* x, double* y, double* s,
+                           lp_info* info, double* times);
+
+lp_status lp_server_stats(lp_server* srv, lp_server_stats_t* out);
+
+/* Drops queued requests, waits for live ones, frees the server.  NULL is a no-op. */
+void lp_server_destroy(lp_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,7 +7,8 @@ vector of Eq. compv.  The computation runs in the CUDA library built from ``csrc
 reached through the C ABI of ``include/lp.h``; this package only marshals arguments.
 
 ``LPSolver`` wraps one context for torch tensors (device memory and streams come from
-PyTorch); the raw entry points are re-exported with their C names.
+PyTorch); ``LPServer`` drives the library's serving loop (continuous batching of many
+instances); the raw entry points are re-exported with their C names.
 """
 from __future__ import annotations
 
@@ -16,7 +17,8 @@ from ._binding import (DTYPE_CODES, LP_CSR, LP_DENSE_COLMAJOR, LP_DENSE_ROWMAJOR
                        lp_info, lp_ipm_solve, lp_normal_matvec, lp_normal_solve, lp_params,
                        lp_params_default, lp_profile, lp_profile_enable, lp_profile_read,
                        lp_residuals, lp_set_params, lp_sketch,
-                       lp_sketch_indices, lp_step, load)
+                       lp_sketch_indices, lp_step, load, lp_footprint_bytes)
+from .server import LPServer
 from .solver import LPSolver
 
 __all__ = [
@@ -24,5 +26,6 @@ __all__ = [
     "lp_destroy", "lp_set_params", "lp_ipm_solve", "lp_normal_solve", "lp_residuals",
     "lp_sketch_indices", "lp_sketch", "lp_factor", "lp_normal_matvec", "lp_step",
     "LP_DENSE_COLMAJOR", "LP_DENSE_ROWMAJOR", "LP_CSR", "LP_F64", "LP_F32", "LP_BF16", "LP_F16",
-    "DTYPE_CODES", "lp_profile", "lp_profile_enable", "lp_profile_read",
+    "DTYPE_CODES", "lp_profile", "lp_profile_enable", "lp_profile_read", "LPServer",
+    "lp_footprint_bytes",
 ]

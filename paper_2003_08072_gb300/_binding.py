@@ -85,6 +85,18 @@ class lp_profile(ctypes.Structure):
         }
 
 
+class lp_server_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+        ("queued", ctypes.c_int64), ("live", ctypes.c_int64), ("peak_live", ctypes.c_int64),
+        ("mem_in_use", ctypes.c_uint64), ("mem_peak", ctypes.c_uint64),
+        ("mem_budget", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class LPError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{status_str(status)}: {msg}")
@@ -118,6 +130,17 @@ _SIGNATURES = {
     "lp_normal_matvec_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _I32, _I64, _I64, _VP, _VP,
                                                 _VP, _VP, _VP]),
     "lp_profile_enable": (ctypes.c_int, [_VP, _I32]),
+    "lp_footprint_bytes": (ctypes.c_uint64, [_I32, _I64, ctypes.c_int, ctypes.c_int, _I64,
+                                             ctypes.POINTER(lp_params), _I32]),
+    "lp_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_uint64, _I32,
+                                        ctypes.POINTER(lp_params)]),
+    "lp_server_submit": (ctypes.c_int, [_VP, _I32, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                                        _VP, _I64, _VP, _VP, ctypes.POINTER(_I64)]),
+    "lp_server_wait_any": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I64)]),
+    "lp_server_result": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, ctypes.POINTER(lp_info),
+                                        ctypes.POINTER(_D)]),
+    "lp_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(lp_server_stats_t)]),
+    "lp_server_destroy": (None, [_VP]),
     "lp_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(lp_profile), _I32]),
 }
 
@@ -254,3 +277,55 @@ def lp_normal_matvec_noalloc(A, a_dtype, m, n, lda, d2, v, y, t=None, stream=Non
     """Context-free A D^2 A^T v that allocates nothing (scratch in a static device array)."""
     _check(load().lp_normal_matvec_noalloc(_p(A), a_dtype, m, n, lda, _p(d2), _p(v), _p(y),
                                            _p(t), _p(stream)))
+
+
+# ---- memory footprint and the serving loop ----------------------------------------------------
+
+def lp_footprint_bytes(m, n, layout, a_dtype, nnz=0, params: Optional[lp_params] = None,
+                       num_sms=0) -> int:
+    prm = params if params is not None else lp_params_default()
+    return int(load().lp_footprint_bytes(m, n, layout, a_dtype, nnz, ctypes.byref(prm), num_sms))
+
+
+def lp_server_create(mem_budget_bytes: int, max_live: int, params: Optional[lp_params] = None):
+    srv = _VP()
+    prm = params if params is not None else lp_params_default()
+    _check(load().lp_server_create(ctypes.byref(srv), int(mem_budget_bytes), int(max_live),
+                                   ctypes.byref(prm)))
+    return srv.value
+
+
+def lp_server_submit(srv, m, n, layout, a_dtype, A_vals, indptr, indices, nnz, b, c) -> int:
+    t = _I64()
+    _check(load().lp_server_submit(srv, m, n, layout, a_dtype, _p(A_vals), _p(indptr),
+                                   _p(indices), nnz, _p(b), _p(c), ctypes.byref(t)))
+    return t.value
+
+
+def lp_server_wait_any(srv, timeout_ms: int):
+    """Ticket of the next finished request, or None after timeout_ms."""
+    t = _I64()
+    st = load().lp_server_wait_any(srv, int(timeout_ms), ctypes.byref(t))
+    if st == LP_ERR_TIMEOUT:
+        return None
+    _check(st)
+    return t.value
+
+
+def lp_server_result(srv, ticket, x, y, s):
+    """(status, lp_info, (queued_s, solve_s, latency_s)); x, y, s host float64 arrays or None."""
+    info = lp_info()
+    times = (_D * 3)()
+    st = load().lp_server_result(srv, ticket, _p(x), _p(y), _p(s), ctypes.byref(info), times)
+    return st, info, (times[0], times[1], times[2])
+
+
+def lp_server_stats(srv) -> lp_server_stats_t:
+    out = lp_server_stats_t()
+    _check(load().lp_server_stats(srv, ctypes.byref(out)))
+    return out
+
+
+def lp_server_destroy(srv):
+    if srv:
+        load().lp_server_destroy(srv)

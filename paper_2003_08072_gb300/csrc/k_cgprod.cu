@@ -403,8 +403,7 @@ int launch_cgprod_t(ColArgs a, int nwarps, int num_sms, int max_grid, cudaStream
   if (S < 2) return -1;
   const size_t smem = (size_t)S * stage + (size_t)S * 8;
   auto kern = k_cgprod<TA, SPW, TC, kPack, keep_default<TA>() && SPW == 1>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess) {
+  if (ensure_dyn_smem((const void*)kern, smem) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }

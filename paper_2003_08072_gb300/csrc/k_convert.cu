@@ -1,4 +1,7 @@
 // Layout and precision conversion of the input matrix, finiteness checks, scalar setters.
+#include <mutex>
+#include <unordered_map>
+
 #include "dev_util.cuh"
 
 namespace lpk {
@@ -191,6 +194,22 @@ cudaError_t launch_apply_W(const int32_t* hb, int ss, const double* u, int64_t n
   if (g < 1) g = 1;
   { note_launch(); k_apply_W<<<(unsigned)g, 256, 0, st>>>(hb, ss, u, n, wu); }
   return cudaGetLastError();
+}
+
+// Dynamic shared-memory limits only ever go up: contexts on other threads may launch the same
+// kernel concurrently with a larger need, and lowering the limit between their attribute call
+// and their launch would make that launch fail.  The limit is raised for any size (not only
+// above 48 KB): the 48 KB default covers static plus dynamic shared memory together.
+cudaError_t ensure_dyn_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> set;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[func];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 }  // namespace lpk

@@ -80,8 +80,7 @@ static int launch_csc_t(CscArgs a, int num_sms, cudaStream_t st) {
   const size_t smem = (size_t)a.m * sizeof(ACC) * (1 + NOUT);
   if (smem > 220 * 1024) return -1;
   auto kern = k_csc<TV, ACC, MODE>;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (ensure_dyn_smem((const void*)kern, smem) != cudaSuccess) return -1;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem) != cudaSuccess ||
       per_sm < 1)

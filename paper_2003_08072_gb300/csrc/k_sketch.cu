@@ -320,15 +320,11 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
                                      cudaStream_t st) {
   const size_t smem = (size_t)m * sizeof(double);
   if (tv == LP_F32) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_gather_csc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+    if (cudaError_t e = ensure_dyn_smem((const void*)k_gather_csc<float>, smem)) return e;
     { note_launch(); k_gather_csc<float><<<w, 256, smem, st>>>(colptr, rowidx, (const float*)vals, m, s, start,
                                               list, d, G, ldg); }
   } else if (tv == LP_F64) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_gather_csc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+    if (cudaError_t e = ensure_dyn_smem((const void*)k_gather_csc<double>, smem)) return e;
     { note_launch(); k_gather_csc<double><<<w, 256, smem, st>>>(colptr, rowidx, (const double*)vals, m, s, start,
                                                list, d, G, ldg); }
   } else {

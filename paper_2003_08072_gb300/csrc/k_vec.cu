@@ -327,12 +327,9 @@ cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, do
 
 cudaError_t symv_set_smem(int m) {
   const int bytes = ((m + 3) & ~3) * 2 * (int)sizeof(double);
-  if (bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_symv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_symv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  }
-  return cudaSuccess;
+  cudaError_t e = ensure_dyn_smem((const void*)k_symv<true>, bytes);
+  if (e != cudaSuccess) return e;
+  return ensure_dyn_smem((const void*)k_symv<false>, bytes);
 }
 
 // ------------------------------------------------------------------------------------

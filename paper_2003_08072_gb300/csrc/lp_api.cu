@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -97,25 +98,82 @@ static lp_status check_params(const lp_params& p, int m) {
   return LP_OK;
 }
 
+// Device memory of a context comes from the device's stream-ordered pool, allocated and freed
+// in order on the context stream (set for the calling thread by AllocStream while lp_create or
+// lp_destroy runs).  Creating and destroying contexts, which the serving loop does for every
+// request, then neither synchronises the device nor hands memory back to the driver.
+static thread_local cudaStream_t t_alloc_stream = nullptr;
+
+struct AllocStream {
+  cudaStream_t prev;
+  explicit AllocStream(cudaStream_t s) : prev(t_alloc_stream) { t_alloc_stream = s; }
+  ~AllocStream() { t_alloc_stream = prev; }
+};
+
+// Keep freed pool memory for reuse (once per device).
+static void keep_pool_memory(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
 template <typename T>
 static lp_status dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), t_alloc_stream);
   if (e != cudaSuccess) {
+    *p = nullptr;
     cudaGetLastError();
-    return fail(LP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return fail(LP_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
   }
   return LP_OK;
 }
 
+// Small pinned host blocks (the context's scalar mirrors) from a process-wide free list.
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;
+constexpr size_t kPinBlock = 512;
+
+static void* pinned_block() {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      void* p = g_pin_free.back();
+      g_pin_free.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, kPinBlock) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void pinned_release(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
 static void dfree(void* p) {
-  if (p) cudaFree(p);
+  if (p) cudaFreeAsync(p, t_alloc_stream);
 }
 
 extern "C" void lp_destroy(lp_ctx* c) {
   if (!c) return;
-  if (c->st) cudaStreamSynchronize(c->st);
+  cudaStreamSynchronize(c->st);
+  AllocStream as(c->st);
   if (c->own_As) dfree(c->As_req);
   dfree(c->A);
   dfree(c->cs2);
@@ -129,8 +187,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
                   c->u, c->Q, c->M, c->X, c->Pinv, c->T, c->C, c->Qsplit, c->sc, c->fl, c->bpart,
                   c->bcnt};
   for (void* p : bufs) dfree(p);
-  if (c->sc_h) cudaFreeHost(c->sc_h);
-  if (c->fl_h) cudaFreeHost(c->fl_h);
+  pinned_release(c->pin_blk);
   for (auto& pr : c->ev_pending) {
     if (pr.a) cudaEventDestroy(pr.a);
     if (pr.b) cudaEventDestroy(pr.b);
@@ -188,8 +245,11 @@ static lp_status alloc_workspace(lp_ctx* c) {
   LP_CU(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), c->st));
   LP_CU(cudaMemsetAsync(c->fl, 0, FL_COUNT * sizeof(int), c->st));
   LP_CU(cudaMemsetAsync(c->bcnt, 0, 16 * sizeof(unsigned), c->st));
-  LP_CU(cudaMallocHost((void**)&c->sc_h, SC_COUNT * sizeof(double)));
-  LP_CU(cudaMallocHost((void**)&c->fl_h, FL_COUNT * sizeof(int)));
+  static_assert(SC_COUNT * sizeof(double) + FL_COUNT * sizeof(int) <= kPinBlock, "pinned block");
+  c->pin_blk = pinned_block();
+  if (!c->pin_blk) return fail(LP_ERR_OOM, "cudaMallocHost of the scalar mirrors failed");
+  c->sc_h = reinterpret_cast<double*>(c->pin_blk);
+  c->fl_h = reinterpret_cast<int*>(reinterpret_cast<char*>(c->pin_blk) + SC_COUNT * sizeof(double));
   LP_CU(symv_set_smem(m));
   return LP_OK;
 }
@@ -323,8 +383,10 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
     lp_destroy(c);
     return s;
   };
+  AllocStream as(c->st);
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) return bail(lp_cuda_fail(e, "cudaGetDevice"));
+  keep_pool_memory(c->dev);
   e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
   if (e != cudaSuccess) return bail(lp_cuda_fail(e, "cudaDeviceGetAttribute"));
 
@@ -355,7 +417,7 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
       if (e == cudaSuccess)
         e = launch_convert_dense(tmp, a_dtype, true, m, n, c->A, a_dtype, c->lda, c->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-      cudaFree(tmp);
+      dfree(tmp);
       if (e != cudaSuccess) return bail(lp_cuda_fail(e, "row-major A"));
     }
     if ((st = check_finite_dev(c, c->A, a_dtype, (int64_t)c->lda * n, "A")) != LP_OK) return bail(st);
@@ -410,7 +472,10 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
     if (ok) {
       // column ids in range: reuse the finiteness flag through a tiny check on host copy
       std::vector<int32_t> hix(nnz);
-      if (cudaMemcpy(hix.data(), ix, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+      if (cudaMemcpyAsync(hix.data(), ix, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(c->st) != cudaSuccess)
+        ok = false;
       for (int64_t k = 0; ok && k < nnz; ++k) ok = hix[k] >= 0 && hix[k] < n;
     }
     if (ok) e = csr_to_csc(ip, ix, vv, a_dtype, m, n, nnz, c->colptr, cur, c->rowidx, c->vals, c->st);
@@ -1100,6 +1165,47 @@ extern "C" lp_status lp_step(lp_ctx* c, double* x, double* y, double* s, const d
     out[3] = c->sc_h[SC_C];
   }
   return LP_OK;
+}
+
+extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, lp_dtype a_dtype,
+                                       int64_t nnz, const lp_params* prm, int32_t num_sms) {
+  if (m < 1 || n < m) return 0;
+  lp_params p;
+  if (prm) p = *prm; else lp_params_default(&p);
+  if (num_sms <= 0) num_sms = 152;
+  const double es = (double)dtype_size(a_dtype);
+  const int s = p.sketch_s > 0 ? p.sketch_s : 4;
+  const int w = p.sketch_w ? p.sketch_w : 4 * m;
+  const int mp = round_up(m, 64);
+  const int nt = mp / 64;
+  const double dn = (double)n, dm = (double)m;
+  double b = 0.0;
+  b += 9 * 8 * dn + 4 * dn + 16 * 8 * dm;                                  // n- and m-vectors
+  b += (double)std::max(coltile_max_grid(num_sms), csc_max_grid(num_sms)) * 2 * dm * 8;
+  b += dn * s * (4 + 4 + 8) + 2.0 * kQCopies * dm * 4 + 3.0 * (w + 1) * 4; // sketch indices
+  b += (double)round_up(m, 2) * w * 8 + (double)w * 8;                     // G, u
+  b += 3.0 * mp * mp * 8 + 2.0 * kNB * kNB * 8 + 2.0 * kNB * mp * 8;      // Q, M, X, factor work
+  b += (double)gram_split(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;
+  b += (SC_COUNT + kMaxRedBlocks * 8) * 8.0 + FL_COUNT * 4 + 64;
+  b += 8 * dm + 8 * dn;                                                    // b, c
+  if (layout != LP_CSR) {
+    const int lda = round_up(m, (int)(16 / dtype_size(a_dtype)));
+    b += (double)lda * dn * es;
+    if (layout == LP_DENSE_ROWMAJOR) b += dm * dn * es;                    // staging copy
+    lp_dtype sd = p.stream_dtype == LP_F64 ? a_dtype : p.stream_dtype;
+    if (sd == LP_F64 && a_dtype == LP_F32) sd = LP_F32;
+    if (sd != a_dtype) {
+      const int ldas = round_up(m, (int)(16 / dtype_size(sd)));
+      b += (double)ldas * dn * dtype_size(sd);
+      if (sd == LP_BF16 || sd == LP_F16) b += 4 * dn;
+    }
+  } else {
+    const double z = (double)std::max<int64_t>(nnz, 0);
+    b += 2 * ((dm + 1) * 8 + z * 4 + z * es) + 8 * dn + (dn + 1) * 8;      // CSR staging + CSC
+    if (p.stream_dtype == LP_F32 && a_dtype == LP_F64) b += 4 * z;
+  }
+  b += 60.0 * 512 + 2.0 * (1 << 20);                                       // pool granularity, slack
+  return (uint64_t)b;
 }
 
 extern "C" lp_status lp_profile_enable(lp_ctx* c, int32_t on) {

@@ -146,6 +146,7 @@ struct lp_ctx {
   int* fl = nullptr;           // device FL_COUNT
   double* bpart = nullptr;     // last-block reduction partials (kMaxRedBlocks * 8)
   unsigned* bcnt = nullptr;    // last-block counters (16)
+  void* pin_blk = nullptr;     // pinned host block holding sc_h and fl_h
   double* sc_h = nullptr;      // pinned host mirror of sc
   int* fl_h = nullptr;         // pinned host mirror of fl
 
@@ -350,6 +351,8 @@ int gram_split(int m, int w, int num_sms);
 // conversions
 cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, int m, int64_t n,
                                  void* dst, lp_dtype ddt, int ldd, cudaStream_t st);
+// Raises (never lowers) a kernel's dynamic shared-memory limit to at least `bytes`.
+cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
 cudaError_t launch_convert_colscaled(const void* src, lp_dtype sdt, int lda, int m, int64_t n,
                                      void* dst, lp_dtype ddt, int ldd, float* cs2,
                                      cudaStream_t st);

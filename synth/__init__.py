@@ -171,3 +171,30 @@ def serving_requests(count: int, m_range=(16, 512), ratio_range=(20, 200), seed:
         n = m * int(rng.integers(ratio_range[0], ratio_range[1] + 1))
         out.append(("dense" if i % 2 == 0 else "sparse", m, n, int(rng.integers(0, 2**31))))
     return out
+
+
+def dense_lp_f32(seed: int, m: int, n: int) -> DenseLP:
+    """Gaussian dense LP as ``dense_lp`` but with A drawn directly in float32 (faster for
+    many large instances; a different random stream than ``dense_lp`` for the same seed)."""
+    rng = np.random.default_rng([seed, 32])
+    At = rng.standard_normal((n, m), dtype=np.float32)
+    x0 = rng.uniform(0.5, 1.5, n)
+    y0 = rng.standard_normal(m)
+    s0 = rng.uniform(0.5, 1.5, n)
+    b = x0 @ At.astype(np.float64)
+    c = At.astype(np.float64) @ y0 + s0
+    return DenseLP(At=At, b=b, c=c, x0=x0, y0=y0, s0=s0)
+
+
+def serving_instance(kind: str, m: int, n: int, seed: int):
+    """One request of the serving stream: a dense Gaussian FP32 LP, or a CSR LP at 1% density
+    (max(1, round(m / 100)) nonzeros per column, column j < m holding row j)."""
+    if kind == "dense":
+        return dense_lp_f32(seed, m, n)
+    return sparse_lp(seed, m, n, nnz_per_col=max(1, int(round(0.01 * m))))
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 5) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson stream of the given rate."""
+    rng = np.random.default_rng([seed, 99])
+    return np.cumsum(rng.exponential(1.0 / rate, count))

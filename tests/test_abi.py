@@ -88,3 +88,28 @@ def test_no_cpu_fallback_in_product_package():
         if fn.endswith(".py"):
             src = open(os.path.join(pkgdir, fn)).read()
             assert not re.search(r"^\s*(from|import)\s+(\.\.)?oracle", src, flags=re.M), fn
+
+
+def test_footprint_bound_is_host_only_and_monotone(lib):
+    """lp_footprint_bytes (admission control of the serving loop) is a pure host computation:
+    zero for invalid shapes, at least the matrix copies it must hold, growing with m, n, the
+    nonzeros and an extra low-precision copy."""
+    import paper_2003_08072_gb300 as pkg
+    from paper_2003_08072_gb300 import _binding as B
+
+    def f(m, n, layout=B.LP_DENSE_COLMAJOR, dt=B.LP_F32, nnz=0, sd=None):
+        p = pkg.lp_params_default()
+        if sd is not None:
+            p.stream_dtype = sd
+        return B.lp_footprint_bytes(m, n, layout, dt, nnz, p, 152)
+
+    assert f(0, 10) == 0 and f(20, 10) == 0
+    base = f(100, 10_000)
+    assert base >= 100 * 10_000 * 4
+    assert f(200, 10_000) > base and f(100, 20_000) > base
+    assert f(100, 10_000, dt=B.LP_F64) >= base + 100 * 10_000 * 4
+    assert f(100, 10_000, sd=B.LP_BF16) >= base + 100 * 10_000 * 2
+    assert f(100, 10_000, layout=B.LP_DENSE_ROWMAJOR) >= base + 100 * 10_000 * 4
+    sp = f(100, 10_000, layout=B.LP_CSR, nnz=40_000)
+    assert f(100, 10_000, layout=B.LP_CSR, nnz=80_000) >= sp + 40_000 * 8
+    assert sp < base

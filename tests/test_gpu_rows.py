@@ -184,7 +184,8 @@ def test_normal_matvec_fp64(case):
 
 
 @pytest.mark.parametrize("sd", ["f32", "bf16", "f16"])
-@pytest.mark.parametrize("m,n", [(300, 20_011), (2000, 6007), (5001, 5003), (8192, 8209)])
+@pytest.mark.parametrize("m,n", [(300, 20_011), (503, 9001), (2000, 6007), (5001, 5003),
+                                 (8192, 8209)])
 def test_normal_matvec_low_precision_stream(sd, m, n):
     """FP32 accumulation over A streamed in the given precision, against the exactly rounded
     matrix in FP64: relative error within 64 u_fp32 sqrt(m) of the |A| D^2 |A|^T |v| scale.
