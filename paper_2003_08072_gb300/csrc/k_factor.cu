@@ -137,53 +137,6 @@ cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* 
 // A diagonal pivot of the Schur complement below 1e-14 of the original diagonal entry of Q is
 // reported as a lost pivot (FL_BREAK).
 
-// Cholesky of a kNB x kNB SPD tile in shared memory (lower triangle, in place), then X = L^{-1}
-// (lower triangular, zeros above).  Needs blockDim.x == 256.  Returns false on a lost pivot.
-// One thread takes each square root and reciprocal (FP64 division and square root are slow
-// on this GPU); everything else multiplies by the broadcast reciprocal.
-__device__ bool chol_inv_tile(double (*P)[kNB + 1], double (*Xs)[kNB + 1], const double* q0) {
-  __shared__ double s_inv[kNB];
-  __shared__ int s_ok;
-  const int tid = threadIdx.x;
-  if (tid == 0) s_ok = 1;
-  for (int p = 0; p < kNB; ++p) {
-    __syncthreads();
-    if (tid == 0) {
-      double d = P[p][p];
-      if (!(d > 1e-14 * q0[p]) || !isfinite(d)) {
-        s_ok = 0;
-        d = fmax(fabs(q0[p]), 1e-300);   // keep the arithmetic finite; the flag aborts the solve
-      }
-      const double l = sqrt(d);
-      P[p][p] = l;
-      s_inv[p] = 1.0 / l;
-    }
-    __syncthreads();
-    const double inv = s_inv[p];
-    if (tid > p && tid < kNB) P[tid][p] *= inv;
-    __syncthreads();
-    for (int e = tid; e < kNB * kNB; e += blockDim.x) {
-      const int i = e / kNB, j = e % kNB;
-      if (j > p && j <= i) P[i][j] -= P[i][p] * P[j][p];
-    }
-  }
-  __syncthreads();
-  // X = L^{-1}, row by row: X_ij = -inv_ii sum_{j<=q<i} L_iq X_qj (j < i), X_ii = inv_ii.
-  // 8 threads per column j share the sum over q and reduce with shuffles.
-  const int j = tid >> 3, part = tid & 7;
-  for (int i = 0; i < kNB; ++i) {
-    double s = 0.0;
-    if (j < i)
-      for (int q = j + part; q < i; q += 8) s = fma(P[i][q], Xs[q][j], s);
-    s += __shfl_xor_sync(kFull, s, 4);
-    s += __shfl_xor_sync(kFull, s, 2);
-    s += __shfl_xor_sync(kFull, s, 1);
-    if (part == 0) Xs[i][j] = (j < i) ? -s * s_inv[i] : (j == i ? s_inv[i] : 0.0);
-    __syncthreads();
-  }
-  return s_ok != 0;
-}
-
 __device__ __forceinline__ void tri_decode(int idx, int& i, int& j) {
   i = 0;
   while ((i + 1) * (i + 2) / 2 <= idx) ++i;
@@ -515,18 +468,6 @@ __global__ void k_add_shift(double* out, const double* Q, int mp, int m, double 
 cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double eps,
                              const double* v, cudaStream_t st) {
   { note_launch(); k_add_shift<<<(m + 255) / 256, 256, 0, st>>>(out, Q, mp, m, eps, v); }
-  return cudaGetLastError();
-}
-
-// Relative diagonal shift M_ii *= (1 + eps): keeps the preconditioner positive definite when
-// the Gram matrix is numerically singular (e.g. colliding CountSketch buckets late in the IPM).
-__global__ void k_shift_diag(double* M, int mp, int m, double eps) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    M[(size_t)i * mp + i] *= (1.0 + eps);
-}
-
-cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t st) {
-  { note_launch(); k_shift_diag<<<(m + 255) / 256, 256, 0, st>>>(M, mp, m, eps); }
   return cudaGetLastError();
 }
 

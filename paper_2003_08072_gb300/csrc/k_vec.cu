@@ -332,38 +332,6 @@ cudaError_t symv_set_smem(int m) {
   return ensure_dyn_smem((const void*)k_symv<false>, bytes);
 }
 
-// ------------------------------------------------------------------------------------
-// CG vector updates
-// ------------------------------------------------------------------------------------
-__global__ void k_cg_axpy(double* dy, double* r, const double* d, const double* q, int m,
-                          const double* sc, const int* fl) {
-  if (fl[FL_DONE]) return;
-  const double al = sc[SC_ALPHA];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    dy[i] = fma(al, d[i], dy[i]);
-    r[i] = fma(-al, q[i], r[i]);
-  }
-}
-
-cudaError_t launch_cg_axpy(double* dy, double* r, const double* d, const double* q, int m,
-                           const double* sc, const int* fl, cudaStream_t st) {
-  { note_launch(); k_cg_axpy<<<(m + 255) / 256, 256, 0, st>>>(dy, r, d, q, m, sc, fl); }
-  return cudaGetLastError();
-}
-
-__global__ void k_cg_dir(double* d, const double* z, int m, const double* sc, const int* fl) {
-  if (fl[FL_DONE]) return;
-  const double be = sc[SC_BETA];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    d[i] = fma(be, d[i], z[i]);
-}
-
-cudaError_t launch_cg_dir(double* d, const double* z, int m, const double* sc, const int* fl,
-                          cudaStream_t st) {
-  { note_launch(); k_cg_dir<<<(m + 255) / 256, 256, 0, st>>>(d, z, m, sc, fl); }
-  return cudaGetLastError();
-}
-
 __global__ void k_vec_ops(int op, double* a, const double* b, const double* c, int m) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     switch (op) {

@@ -184,7 +184,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   void* bufs[] = {c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G,
-                  c->u, c->Q, c->M, c->X, c->Pinv, c->T, c->C, c->Qsplit, c->sc, c->fl, c->bpart,
+                  c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
                   c->bcnt};
   for (void* p : bufs) dfree(p);
   pinned_release(c->pin_blk);
@@ -231,9 +231,6 @@ static lp_status alloc_workspace(lp_ctx* c) {
   LP_TRY(dalloc(&c->Q, (size_t)c->mp * c->mp));
   LP_TRY(dalloc(&c->M, (size_t)c->mp * c->mp));
   LP_TRY(dalloc(&c->X, (size_t)c->mp * c->mp));
-  LP_TRY(dalloc(&c->Pinv, (size_t)2 * kNB * kNB));
-  LP_TRY(dalloc(&c->T, (size_t)kNB * c->mp));
-  LP_TRY(dalloc(&c->C, (size_t)c->mp * kNB));
   c->qsplit = gram_split(m, c->w, c->num_sms);
   const int nt = c->mp / 64;
   LP_TRY(dalloc(&c->Qsplit, (size_t)c->qsplit * (nt * (nt + 1) / 2) * 64 * 64));
@@ -1184,7 +1181,7 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   b += (double)std::max(coltile_max_grid(num_sms), csc_max_grid(num_sms)) * 2 * dm * 8;
   b += dn * s * (4 + 4 + 8) + 2.0 * kQCopies * dm * 4 + 3.0 * (w + 1) * 4; // sketch indices
   b += (double)round_up(m, 2) * w * 8 + (double)w * 8;                     // G, u
-  b += 3.0 * mp * mp * 8 + 2.0 * kNB * kNB * 8 + 2.0 * kNB * mp * 8;      // Q, M, X, factor work
+  b += 3.0 * mp * mp * 8;                                                  // Q, M, X
   b += (double)gram_split(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;
   b += (SC_COUNT + kMaxRedBlocks * 8) * 8.0 + FL_COUNT * 4 + 64;
   b += 8 * dm + 8 * dn;                                                    // b, c

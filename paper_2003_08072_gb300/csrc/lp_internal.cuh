@@ -134,9 +134,6 @@ struct lp_ctx {
   double* Q = nullptr;         // mp x mp row-major (full symmetric)
   double* M = nullptr;         // Q^{-1} as double-float pairs (hi, lo: two mp x mp float matrices)
   double* X = nullptr;         // L^{-1} work buffer of the factor, mp x mp
-  double* Pinv = nullptr;      // kNB x kNB
-  double* T = nullptr;         // kNB x mp
-  double* C = nullptr;         // mp x kNB
   double* Qsplit = nullptr;    // split-k partials of the Gram product
   int qsplit = 1;
   double shift = 0.0;          // relative diagonal shift used by the last factorization
@@ -290,7 +287,6 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
 // factor
 cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* Q, double* Qsplit,
                         int split, cudaStream_t st);
-cudaError_t launch_shift_diag(double* M, int mp, int m, double eps, cudaStream_t st);
 cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double eps,
                              const double* v, cudaStream_t st);
 cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
@@ -318,10 +314,6 @@ cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, do
 cudaError_t symv_set_smem(int m);
 int coltile_max_grid(int num_sms);
 int csc_max_grid(int num_sms);
-cudaError_t launch_cg_axpy(double* dy, double* r, const double* d, const double* q, int m,
-                           const double* sc, const int* fl, cudaStream_t st);
-cudaError_t launch_cg_dir(double* d, const double* z, int m, const double* sc, const int* fl,
-                          cudaStream_t st);
 cudaError_t launch_vec_ops(int op, double* a, const double* b, const double* c, int m,
                            const double* sc, cudaStream_t st);
 enum VecOp { VOP_COPY = 0, VOP_ZERO = 1, VOP_ADD = 2, VOP_SUB = 3, VOP_NEG = 4, VOP_ONES = 5 };
