@@ -91,6 +91,11 @@ def dist_setup():
     return rank, world, local
 
 
+def shard(count: int, rank: int, world: int):
+    """Requests of the serving stream this rank submits: i = rank, rank + world, ..."""
+    return list(range(rank, count, world))
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -488,7 +493,7 @@ def run_serving(args, rank, world, local):
 
     pkg.load(build_if_missing=False)
     torch.cuda.set_device(local)
-    mine = [i for i in range(len(insts)) if i % world == rank]
+    mine = shard(len(insts), rank, world)
     prm = pkg.lp_params_default()
     prm.stream_dtype = pkg.LP_BF16
     runs = []

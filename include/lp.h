@@ -56,6 +56,8 @@ typedef enum {
 
 typedef enum { LP_F64 = 0, LP_F32 = 1, LP_BF16 = 2, LP_F16 = 3 } lp_dtype;
 
+typedef enum { LP_INNER_CG = 0, LP_INNER_RICHARDSON = 1 } lp_inner_solver;
+
 /* Parameters of Algorithms 1 and 2.  Defaults from lp_params_default(). */
 typedef struct {
   double tol;            /* stop when ||r_p||/(1+||b||), ||r_d||/(1+||c||), n mu/(1+|c^T x|) <= tol (1e-8) */
@@ -76,6 +78,11 @@ typedef struct {
                             fails to halve ||f|| (or refine_max rounds pass) the solve streams the
                             input-precision copy from then on (lp_info.stream_switch_iter). */
   int32_t cg_batch;      /* CG iterations enqueued between host checks of the stop flag (4) */
+  int32_t inner_solver;  /* LP_INNER_CG (0): Alg. 1 step 3; LP_INNER_RICHARDSON (1): the preconditioned
+                            Richardson iteration of App. A (dy += Q^{-1}(p - A D^2 A^T dy)), same stop
+                            rule; it converges only when ||I - Q^{-1/2} A D^2 A^T Q^{-1/2}|| < 1, i.e.
+                            for a sketch much wider than 4m, and a diverging run ends the solve with
+                            LP_ERR_NOT_CONVERGED (0) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */

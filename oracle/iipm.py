@@ -47,6 +47,7 @@ class Params:
     seed: int = 0
     refine_max: int = 6         # steps of the FP64 refinement of Q^{-1} r~ (Sec. 4, Eq. compv)
     cg_theory_rule: bool = True # also stop only once ||f|| <= gamma sigma sqrt(mu)/(4 sqrt(n)) (Sec. 4)
+    inner: str = "cg"           # "cg" (Alg. 1 step 3) or "richardson" (App. A)
 
 
 # --------------------------------------------------------------------------
@@ -246,6 +247,35 @@ def cg_precond_alt(matvec: Callable, p, Qmh, tol: float, max_iter: int) -> CGRes
     return CGResult(dy=Qmh @ z, iters=it, rho=hist, converged=converged)
 
 
+def richardson(matvec: Callable, p, Qmh, max_iter: int, tol: float = 0.0,
+               abs_tol: float = math.inf) -> CGResult:
+    """Richardson's iteration of App. A in place of Alg. 1 step 3.
+
+    z^0 = 0 and z^j = z^{j-1} + Q^{-1/2} (p - A D^2 A^T Q^{-1/2} z^{j-1}); the
+    output is dy = Q^{-1/2} z^t.  ``rho`` holds ||f~^(j)||^2 with
+    f~^(j) = Q^{-1/2} (A D^2 A^T Q^{-1/2} z^j - p), the residual of Lemma
+    recursive.  App. A runs a fixed number t of steps; here it also stops, like
+    CG, once ||f~^(j)|| <= min(tol ||f~^(0)||, abs_tol) (tol = 0: exactly
+    max_iter steps).  ``Qmh`` is Q^{-1/2}.
+    """
+    z = np.zeros_like(p)
+    f = -(Qmh @ p)                      # f~^(0) = -Q^{-1/2} p
+    rho = float(f @ f)
+    hist = [rho]
+    thresh = min(tol * math.sqrt(rho), abs_tol)
+    it = 0
+    converged = False
+    while it < max_iter:
+        z = z + Qmh @ (p - matvec(Qmh @ z))
+        f = Qmh @ (matvec(Qmh @ z) - p)
+        it += 1
+        hist.append(float(f @ f))
+        if math.sqrt(hist[-1]) <= thresh:
+            converged = True
+            break
+    return CGResult(dy=Qmh @ z, iters=it, rho=hist, converged=converged)
+
+
 # --------------------------------------------------------------------------
 # Alg. 2 step (d): correction vector v and the corrected direction
 # --------------------------------------------------------------------------
@@ -418,8 +448,12 @@ def normal_solve_sketch(A, x, s, p, k, prm: Params):
     G = sketch_ADW(A, d, bucket, sign, w)
     R = factor_R(G)
     mv = lambda v: normal_matvec(A, d2, v)
-    cg = pcg(mv, p, lambda r: q_inverse_apply(R, r), prm.cg_tol, prm.cg_max_iter,
-             abs_tol=cg_abs_threshold(x, s, prm))
+    if prm.inner == "richardson":
+        cg = richardson(mv, p, q_inv_half_svd(G), prm.cg_max_iter, prm.cg_tol,
+                        abs_tol=cg_abs_threshold(x, s, prm))
+    else:
+        cg = pcg(mv, p, lambda r: q_inverse_apply(R, r), prm.cg_tol, prm.cg_max_iter,
+                 abs_tol=cg_abs_threshold(x, s, prm))
     rtil = mv(cg.dy) - p
     u, qhat, steps = correction_u(G, R, rtil, prm.refine_max)
     Wu = apply_W(u, bucket, sign)

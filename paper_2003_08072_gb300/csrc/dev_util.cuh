@@ -168,6 +168,20 @@ __device__ __forceinline__ bool grid_min_last(double& v, double* bpart, unsigned
   return true;
 }
 
+// Step length of one iteration from d^T q: CG's alpha = rho / d^T q (Alg. 1 step 3), or the
+// unit step of Richardson's iteration (App. A), whose update dy += M (p - K dy) is the same
+// iteration with alpha = 1 and beta = 0.  A non-positive or non-finite d^T q stops the solve.
+__device__ __forceinline__ void set_cg_alpha(double dq, double* sc, int* fl) {
+  sc[SC_DQ] = dq;
+  if (!(dq > 0.0) || !isfinite(dq)) {
+    fl[FL_NUMERIC] = 1;
+    fl[FL_DONE] = 1;
+    sc[SC_ALPHA] = 0.0;
+  } else {
+    sc[SC_ALPHA] = fl[FL_RICH] ? 1.0 : sc[SC_RHO] / dq;
+  }
+}
+
 }  // namespace lpk
 
 namespace lpk {

@@ -13,12 +13,14 @@
 // Per group the warps form the TC column dots a_i^T v (rows split across warps as slices of
 // 32 lanes x 16 bytes, v in registers), reduce them across the CTA through shared memory,
 // weight them with D^2 (FP32, times the column scales of a scaled 16-bit copy), and add
-// a_i * coef_i into per-thread row accumulators.  Arithmetic runs on packed pairs of rows
-// (fma.rn.f32x2: half the FMA instructions) when built with LP_CGPROD_PACK=1, and with
-// LP_CGPROD_KEEP=1 a warp with one row slice keeps the unpacked group in registers between
-// the two phases instead of reading and unpacking it twice.  The
-// CTA's row sums then go to the q buffers with atomics (the last CTA forms d^T q and alpha, as
-// in the register-tiled pass) or to per-CTA partials.
+// a_i * coef_i into per-thread row accumulators.  With one row slice per warp, 16-bit groups
+// stay unpacked in registers between the two phases instead of being read and unpacked twice.
+// For FP32 copies the products of four groups (32 columns) are summed first and added to the
+// accumulator with an error-free TwoSum (the error term kept in a second accumulator), so a row
+// sum over the ~n/grid columns a CTA sees loses no more than a few FP32 units; the CTA sums go
+// to q with FP64 atomics.  Keeping the FP32-accumulated product near FP32 accuracy keeps CG's residual
+// recurrence close to the true residual, which spares most FP64 refinement rounds.  The last
+// CTA forms d^T q and alpha; without a q buffer the sums go to per-CTA partials.
 //
 // Every wait on an mbarrier is bounded by the global timer; a wait that gives up sets
 // FL_TIMEOUT and the CTA carries on without the data (the host turns the flag into
@@ -96,65 +98,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   }
 }
 
-// Packed pairs of FP32 values in one 64-bit register (first value in the low half) and the
-// paired FMA of sm_100 and later: d = a * b + c element by element, each rounded as fmaf.
-__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
-  return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-}
-
-__device__ __forceinline__ float elem2(uint64_t v, int which) {
-  return __uint_as_float(which ? (unsigned)(v >> 32) : (unsigned)v);
-}
-
-__device__ __forceinline__ float sum2(uint64_t v) { return elem2(v, 0) + elem2(v, 1); }
-
-[[maybe_unused]] __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-// 16 bytes of TA -> VEC/2 packed pairs of FP32 (elements 2p, 2p + 1 in pair p).
-template <typename TA>
-__device__ __forceinline__ void unpack_pairs(const uint4& r, uint64_t (&o)[VecN<TA>::N / 2]) {
-  if constexpr (sizeof(TA) == 4) {
-    o[0] = ((uint64_t)r.y << 32) | r.x;
-    o[1] = ((uint64_t)r.w << 32) | r.z;
-  } else {
-    const unsigned w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if constexpr (std::is_same<TA, __nv_bfloat16>::value) {
-        // a bf16 is the upper half of an FP32
-        o[i] = ((uint64_t)(w[i] & 0xffff0000u) << 32) | (w[i] << 16);
-      } else {
-        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
-        o[i] = pack2(f.x, f.y);
-      }
-    }
-  }
-}
-
-// 16 bytes of TA -> VEC FP32 values, or VEC/2 packed pairs
-template <typename TA, bool PACK, typename Acc>
-__device__ __forceinline__ void unpack_acc(const uint4& r, Acc (&o)[PACK ? VecN<TA>::N / 2 : VecN<TA>::N]) {
-  if constexpr (PACK) unpack_pairs<TA>(r, o);
-  else unpack<TA, float>(r, o);
-}
-
-template <bool PACK, typename Acc, int NA>
-__device__ __forceinline__ float acc_elem(const Acc (&y)[NA], int e) {
-  if constexpr (PACK) return elem2(y[e / 2], e & 1);
-  else return y[e];
-}
-
 }  // namespace
 
 // Shared memory: S stages of TC * lda elements, then S mbarriers.
-template <typename TA, int SPW, int TC, bool PACK, bool KEEP>
+template <typename TA, int SPW, int TC, bool KEEP>
 __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroups) {
   constexpr int VEC = VecN<TA>::N;
-  constexpr int NP = VEC / 2;
+  constexpr bool COMP = sizeof(TA) == 4;   // compensated row sums for FP32 copies
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ float red[2][16][TC];
   __shared__ int s_timeout;
@@ -185,17 +135,16 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
     for (int i = 0; i < std::min(S - 1, my_groups); ++i) issue(i, i);
   }
 
-  // v and the row accumulators: VEC values per slice, as VEC/2 packed pairs with PACK
-  using Acc = typename std::conditional<PACK, uint64_t, float>::type;
-  constexpr int NA = PACK ? NP : VEC;
-  Acc vr[SPW][NA], yr[SPW][NA];
+  // v and the row accumulators (g: partial sums of the last groups, yc: TwoSum error terms of
+  // the compensated sums)
+  constexpr int kFlush = 4;
+  float vr[SPW][VEC], yr[SPW][VEC], yc[COMP ? SPW : 1][VEC], g[COMP ? SPW : 1][VEC];
   int rowb[SPW];
   bool rok[SPW];
 #pragma unroll
   for (int sl = 0; sl < SPW; ++sl) {
     rowb[sl] = ((warp * SPW + sl) * 32 + lane) * VEC;
     rok[sl] = rowb[sl] < a.m;
-    float vv[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int row = rowb[sl] + e;
@@ -208,16 +157,11 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
           x = a.v[row];
         }
       }
-      vv[e] = (float)x;
-    }
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      if constexpr (PACK) {
-        vr[sl][j] = pack2(vv[2 * j], vv[2 * j + 1]);
-        yr[sl][j] = 0ull;
-      } else {
-        vr[sl][j] = vv[j];
-        yr[sl][j] = 0.f;
+      vr[sl][e] = (float)x;
+      yr[sl][e] = 0.f;
+      if constexpr (COMP) {
+        yc[sl][e] = 0.f;
+        g[sl][e] = 0.f;
       }
     }
   }
@@ -239,28 +183,26 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
     const float w = cok ? a.d2f[mycol] : 0.f;
     // column dots from the staged group; with KEEP the unpacked group stays in registers for
     // the accumulation below instead of being read and unpacked a second time
-    Acc kept[KEEP ? TC : 1][KEEP ? SPW : 1][NA];
+    float kept[KEEP ? TC : 1][KEEP ? SPW : 1][VEC];
     float pd[TC];
 #pragma unroll
     for (int c = 0; c < TC; ++c) {
-      Acc acc{};
+      float acc = 0.f;
       if (c < ncols) {
 #pragma unroll
         for (int sl = 0; sl < SPW; ++sl) {
           if (!rok[sl]) continue;
           const uint4 r = *reinterpret_cast<const uint4*>(st + (size_t)c * a.lda + rowb[sl]);
-          Acc av[NA];
-          unpack_acc<TA, PACK>(r, av);
+          float av[VEC];
+          unpack<TA, float>(r, av);
 #pragma unroll
-          for (int j = 0; j < NA; ++j) {
-            if constexpr (KEEP) kept[c][sl][j] = av[j];
-            if constexpr (PACK) acc = fma2(av[j], vr[sl][j], acc);
-            else acc = fmaf(av[j], vr[sl][j], acc);
+          for (int e = 0; e < VEC; ++e) {
+            if constexpr (KEEP) kept[c][sl][e] = av[e];
+            acc = fmaf(av[e], vr[sl][e], acc);
           }
         }
       }
-      if constexpr (PACK) pd[c] = sum2(acc);
-      else pd[c] = acc;
+      pd[c] = acc;
     }
     const float wsum = warp_transpose_reduce<TC, float>(pd, lane);
     if (lane < TC) red[i & 1][warp][lane] = wsum;
@@ -281,19 +223,34 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
 #pragma unroll
       for (int sl = 0; sl < SPW; ++sl) {
         if (!rok[sl]) continue;
-        Acc av[NA];
+        float av[VEC];
         if constexpr (KEEP) {
 #pragma unroll
-          for (int j = 0; j < NA; ++j) av[j] = kept[c][sl][j];
+          for (int e = 0; e < VEC; ++e) av[e] = kept[c][sl][e];
         } else {
           const uint4 r = *reinterpret_cast<const uint4*>(st + (size_t)c * a.lda + rowb[sl]);
-          unpack_acc<TA, PACK>(r, av);
+          unpack<TA, float>(r, av);
         }
 #pragma unroll
-        for (int j = 0; j < NA; ++j) {
-          if constexpr (PACK) yr[sl][j] = fma2(pack2(cc, cc), av[j], yr[sl][j]);
-          else yr[sl][j] = fmaf(cc, av[j], yr[sl][j]);
+        for (int e = 0; e < VEC; ++e) {
+          if constexpr (COMP) g[sl][e] = fmaf(cc, av[e], g[sl][e]);
+          else yr[sl][e] = fmaf(cc, av[e], yr[sl][e]);
         }
+      }
+    }
+    if constexpr (COMP) {
+      // every kFlush groups (and after the last) the partial sum joins the accumulator
+      if ((i + 1) % kFlush == 0 || i + 1 == my_groups) {
+#pragma unroll
+        for (int sl = 0; sl < SPW; ++sl)
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            float t, err;
+            two_sum(yr[sl][e], g[sl][e], t, err);
+            yr[sl][e] = t;
+            yc[sl][e] += err;
+            g[sl][e] = 0.f;
+          }
       }
     }
     prev_stage = stage;
@@ -313,16 +270,20 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
     }
     __syncthreads();
   }
+  auto row_sum = [&](int sl, int e) -> double {
+    if constexpr (COMP) return (double)yr[sl][e] + (double)yc[sl][e];
+    else return (double)yr[sl][e];
+  };
 
   if (a.qacc) {
     // kQCopies copies of q spread the atomic traffic over more L2 lines
-    float* qc = a.qacc + (size_t)(blockIdx.x % kQCopies) * a.m;
+    double* qc = a.qacc + (size_t)(blockIdx.x % kQCopies) * a.m;
 #pragma unroll
     for (int sl = 0; sl < SPW; ++sl)
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         const int row = rowb[sl] + e;
-        if (rok[sl] && row < a.m) atomicAdd(&qc[row], acc_elem<PACK>(yr[sl], e));
+        if (rok[sl] && row < a.m) atomicAdd(&qc[row], row_sum(sl, e));
       }
     // last CTA: d^T q and alpha (no waiting: the last CTA to arrive does the work)
     __shared__ bool s_last;
@@ -334,22 +295,15 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
     __threadfence();
     double dq[1] = {0.0};
     for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
-      float qi = 0.f;
+      double qi = 0.0;
 #pragma unroll
       for (int k = 0; k < kQCopies; ++k) qi += __ldcg(&a.qacc[(size_t)k * a.m + i]);
-      dq[0] += a.dnew[i] * (double)qi;
+      dq[0] += a.dnew[i] * qi;
     }
     block_sum<1>(dq);
     if (threadIdx.x == 0) {
       *a.cnt = 0u;
-      a.scw[SC_DQ] = dq[0];
-      if (!(dq[0] > 0.0) || !isfinite(dq[0])) {
-        a.flw[FL_NUMERIC] = 1;
-        a.flw[FL_DONE] = 1;
-        a.scw[SC_ALPHA] = 0.0;
-      } else {
-        a.scw[SC_ALPHA] = a.scw[SC_RHO] / dq[0];
-      }
+      set_cg_alpha(dq[0], a.scw, a.flw);
     }
     return;
   }
@@ -359,7 +313,7 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int row = rowb[sl] + e;
-      if (rok[sl] && row < a.m) part[(size_t)blockIdx.x * a.m + row] = acc_elem<PACK>(yr[sl], e);
+      if (rok[sl] && row < a.m) part[(size_t)blockIdx.x * a.m + row] = (float)row_sum(sl, e);
     }
 }
 
@@ -367,22 +321,13 @@ namespace {
 
 constexpr size_t kSmemBudget = 200 * 1024;   // dynamic shared memory per SM used by the pass
 
-// Inner-loop variants: PACK (paired FP32 FMAs), KEEP (unpacked group kept in registers when a
-// warp has one row slice).  Measured on GB300 (m = 1000 and 2000, n = 200000 and 500000):
-// paired FMAs are slower for every type; keeping the group is 15-20% faster for 16-bit types
-// and slower for FP32, so the default keeps it for 16-bit types only; groups of 16 columns
-// were slower than groups of 8.  LP_CGPROD_PACK / LP_CGPROD_KEEP (0 or 1) override.
-#ifndef LP_CGPROD_PACK
-#define LP_CGPROD_PACK 0
-#endif
-constexpr bool kPack = LP_CGPROD_PACK != 0;
+// 16-bit groups are kept unpacked in registers between the two phases (KEEP).  Measured on
+// GB300 (m = 1000 and 2000, n = 200000 and 500000): keeping the group is 15-20% faster for
+// 16-bit types and slower for FP32 (whose registers go to the compensated sums instead);
+// paired FP32 FMAs (fma.rn.f32x2) and groups of 16 columns were slower.
 template <typename TA>
 constexpr bool keep_default() {
-#ifdef LP_CGPROD_KEEP
-  return LP_CGPROD_KEEP != 0;
-#else
   return sizeof(TA) == 2;
-#endif
 }
 
 template <typename TA, int SPW, int TC>
@@ -402,7 +347,7 @@ int launch_cgprod_t(ColArgs a, int nwarps, int num_sms, int max_grid, cudaStream
   }
   if (S < 2) return -1;
   const size_t smem = (size_t)S * stage + (size_t)S * 8;
-  auto kern = k_cgprod<TA, SPW, TC, kPack, keep_default<TA>() && SPW == 1>;
+  auto kern = k_cgprod<TA, SPW, TC, keep_default<TA>() && SPW == 1>;
   if (ensure_dyn_smem((const void*)kern, smem) != cudaSuccess) {
     cudaGetLastError();
     return -1;

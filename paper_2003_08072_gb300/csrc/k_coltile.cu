@@ -144,13 +144,13 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
   if constexpr (MODE == MODE_NORMAL && std::is_same<ACC, float>::value) {
     if (a.qacc) {
       // kQCopies copies of q spread the atomic traffic over more L2 lines
-      float* qc = a.qacc + (size_t)(blockIdx.x % kQCopies) * a.m;
+      double* qc = a.qacc + (size_t)(blockIdx.x % kQCopies) * a.m;
 #pragma unroll
       for (int sl = 0; sl < SPW; ++sl)
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
           const int row = rowb[sl] + e;
-          if (rok[sl] && row < a.m) atomicAdd(&qc[row], yr[0][sl][e]);
+          if (rok[sl] && row < a.m) atomicAdd(&qc[row], (double)yr[0][sl][e]);
         }
       // last CTA: d^T q and alpha (no waiting: the last CTA to arrive does the work)
       __shared__ bool s_last;
@@ -162,22 +162,15 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
       __threadfence();
       double dq[1] = {0.0};
       for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
-        float qi = 0.f;
+        double qi = 0.0;
 #pragma unroll
         for (int k = 0; k < kQCopies; ++k) qi += __ldcg(&a.qacc[(size_t)k * a.m + i]);
-        dq[0] += a.dnew[i] * (double)qi;
+        dq[0] += a.dnew[i] * qi;
       }
       block_sum<1>(dq);
       if (threadIdx.x == 0) {
         *a.cnt = 0u;
-        a.scw[SC_DQ] = dq[0];
-        if (!(dq[0] > 0.0) || !isfinite(dq[0])) {
-          a.flw[FL_NUMERIC] = 1;
-          a.flw[FL_DONE] = 1;
-          a.scw[SC_ALPHA] = 0.0;
-        } else {
-          a.scw[SC_ALPHA] = a.scw[SC_RHO] / dq[0];
-        }
+        set_cg_alpha(dq[0], a.scw, a.flw);
       }
       return;
     }

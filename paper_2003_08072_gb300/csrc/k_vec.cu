@@ -60,15 +60,7 @@ __global__ void __launch_bounds__(1024) k_reduce(RedArgs a) {
       if (a.mode == RED_RESID) {
         a.sc[SC_RP2] = v[0];
       } else {
-        const double dq = v[0];
-        a.sc[SC_DQ] = dq;
-        if (!(dq > 0.0) || !isfinite(dq)) {
-          a.fl[FL_NUMERIC] = 1;
-          a.fl[FL_DONE] = 1;
-          a.sc[SC_ALPHA] = 0.0;
-        } else {
-          a.sc[SC_ALPHA] = a.sc[SC_RHO] / dq;
-        }
+        set_cg_alpha(v[0], a.sc, a.fl);
       }
     }
   }
@@ -171,8 +163,8 @@ struct SymvArgs {
   const double* q;
   const double* d;
   double* dy;
-  const float* qf;     // q accumulated in FP32 (instead of q)
-  float* qzero;        // zeroed by CTA 0 for the next CG product
+  const double* qf;    // q accumulated in kQCopies atomic copies (instead of q)
+  double* qzero;       // zeroed by CTA 0 for the next CG product
 };
 
 // DF: M holds double-float pairs (Mh = (float*)M, Ml = Mh + mp^2) and the row sums run on the
@@ -191,10 +183,10 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
       if (a.rold) {
         double qi;
         if (a.qf) {
-          float qs = 0.f;
+          double qs = 0.0;
 #pragma unroll
           for (int k = 0; k < kQCopies; ++k) qs += a.qf[(size_t)k * a.m + i];
-          qi = (double)qs;
+          qi = qs;
         } else {
           qi = a.q[i];
         }
@@ -204,7 +196,7 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
           a.dy[i] = fma(al, a.d[i], a.dy[i]);
           if (a.qzero)
 #pragma unroll
-            for (int k = 0; k < kQCopies; ++k) a.qzero[(size_t)k * a.m + i] = 0.f;
+            for (int k = 0; k < kQCopies; ++k) a.qzero[(size_t)k * a.m + i] = 0.0;
         }
       } else {
         v = a.r[i];
@@ -278,9 +270,14 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
   } else {
     const int it = a.fl[FL_ITERS] + 1;
     a.fl[FL_ITERS] = it;
-    a.sc[SC_BETA] = rho / a.sc[SC_RHO];
+    const bool rich = a.fl[FL_RICH] != 0;
+    a.sc[SC_BETA] = rich ? 0.0 : rho / a.sc[SC_RHO];
     a.sc[SC_RHO] = rho;
     if (rho <= a.sc[SC_THR2] || it >= a.fl[FL_MAXIT]) a.fl[FL_DONE] = 1;
+    if (rich && rho > 1e12 * a.sc[SC_RHO0]) {   // ||f|| grew 1e6-fold: the iteration diverges
+      a.fl[FL_DIVERGED] = 1;
+      a.fl[FL_DONE] = 1;
+    }
   }
 }
 
@@ -298,7 +295,7 @@ cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, dou
 cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* rold,
                                 const double* q, const double* d, double* dy, double* rnew,
                                 double* z, double* sc, int* fl, double* bpart, unsigned* bcnt,
-                                cudaStream_t st, const float* qf, float* qzero) {
+                                cudaStream_t st, const double* qf, double* qzero) {
   SymvArgs a{M, mp, m, rnew, z, sc, fl, bpart, bcnt, SYMV_CG_STEP, 0.0, rold, q, d, dy, qf, qzero};
   const size_t smem = (size_t)((m + 3) & ~3) * 2 * sizeof(double);
   { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a); }

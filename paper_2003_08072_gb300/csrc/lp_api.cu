@@ -79,6 +79,7 @@ lp_status lp_params_default(lp_params* p) {
   p->seed = 0;
   p->stream_dtype = LP_F64;
   p->cg_batch = 4;
+  p->inner_solver = LP_INNER_CG;
   return LP_OK;
 }
 
@@ -91,6 +92,8 @@ static lp_status check_params(const lp_params& p, int m) {
   if (p.cg_max_iter < 1 || p.ipm_max_iter < 0 || p.refine_max < 0 || p.cg_batch < 1)
     return fail(LP_ERR_ARG, "invalid iteration caps");
   if (p.sketch_s < 1 || p.sketch_w < 0) return fail(LP_ERR_ARG, "invalid sketch size");
+  if (p.inner_solver != LP_INNER_CG && p.inner_solver != LP_INNER_RICHARDSON)
+    return fail(LP_ERR_ARG, "inner_solver must be LP_INNER_CG or LP_INNER_RICHARDSON");
   const int w = p.sketch_w ? p.sketch_w : 4 * m;
   if (w % p.sketch_s != 0) return fail(LP_ERR_ARG, "sketch_w must be a multiple of sketch_s");
   if (w < m) return fail(LP_ERR_ARG, "sketch_w must be >= m");
@@ -530,7 +533,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
                              int red_mode, double* out, const double* p0, int skip_if_done,
                              bool record_mv = false, const double* dz = nullptr,
                              const double* dold = nullptr, double* dnew = nullptr,
-                             float* qacc = nullptr, bool weight_in_d2f = false) {
+                             double* qacc = nullptr, bool weight_in_d2f = false) {
   int nblk;
   bool acc64;
   cudaEvent_t ea = nullptr, eb = nullptr;
@@ -805,6 +808,11 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
   const double thr2 = isfinite(abs_thr) ? abs_thr * abs_thr : INFINITY;
   LP_CU(launch_set(c->sc, SC_THR2, thr2, c->fl, FL_MAXIT, max_iter, c->st));
   LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_NUMERIC, 0, c->st));
+  // Richardson's iteration (App. A) replaces CG for the normal equations only; the solve for
+  // (A D W)^dagger r~ (op 1) always runs CG
+  const bool rich = op == 0 && c->prm.inner_solver == LP_INNER_RICHARDSON;
+  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_RICH, rich ? 1 : 0, c->st));
+  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_DIVERGED, 0, c->st));
   LP_CU(launch_symv_init(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt, rel_tol,
                          c->st));
   // d starts at 0 so that the first fused direction update (beta = 0) gives d = z
@@ -814,8 +822,8 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
   double* dbuf[2] = {c->dd, c->d_alt};
   // FP32-accumulated dense products reduce themselves into qbuf with atomics
   const bool atomic_q = (op == 0) && !c->sparse && c->s_dtype != LP_F64;
-  float* qbuf[2] = {c->qf, c->qf + (size_t)kQCopies * m};
-  if (atomic_q) LP_CU(cudaMemsetAsync(c->qf, 0, (size_t)kQCopies * m * sizeof(float), c->st));
+  double* qbuf[2] = {c->qf, c->qf + (size_t)kQCopies * m};
+  if (atomic_q) LP_CU(cudaMemsetAsync(c->qf, 0, (size_t)kQCopies * m * sizeof(double), c->st));
   int done_before = 0;
   int j = 0;
   for (;;) {
@@ -842,6 +850,9 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
   if (rho0_out) *rho0_out = c->sc_h[SC_RHO0];
   if (rho_out) *rho_out = c->sc_h[SC_RHO];
   if (c->fl_h[FL_NUMERIC]) return fail(LP_ERR_NUMERIC, "CG met non-positive curvature or NaN");
+  if (c->fl_h[FL_DIVERGED])
+    return fail(LP_ERR_NOT_CONVERGED,
+                "Richardson iteration diverges: ||I - Q^-1/2 A D^2 A^T Q^-1/2|| >= 1 (widen the sketch)");
   return LP_OK;
 }
 
@@ -1179,7 +1190,7 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   double b = 0.0;
   b += 9 * 8 * dn + 4 * dn + 16 * 8 * dm;                                  // n- and m-vectors
   b += (double)std::max(coltile_max_grid(num_sms), csc_max_grid(num_sms)) * 2 * dm * 8;
-  b += dn * s * (4 + 4 + 8) + 2.0 * kQCopies * dm * 4 + 3.0 * (w + 1) * 4; // sketch indices
+  b += dn * s * (4 + 4 + 8) + 2.0 * kQCopies * dm * 8 + 3.0 * (w + 1) * 4; // sketch indices, q
   b += (double)round_up(m, 2) * w * 8 + (double)w * 8;                     // G, u
   b += 3.0 * mp * mp * 8;                                                  // Q, M, X
   b += (double)gram_split(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;

@@ -49,6 +49,8 @@ enum Flag {
   FL_BREAK,      // non-positive pivot in the factorization
   FL_MAXIT,      // CG iteration cap of the current solve
   FL_TIMEOUT,    // a bounded wait in a kernel gave up
+  FL_RICH,       // the running solve is Richardson's iteration (App. A): alpha = 1, beta = 0
+  FL_DIVERGED,   // Richardson's residual grew past 1e6 times its start
   FL_COUNT = 8
 };
 
@@ -111,7 +113,7 @@ struct lp_ctx {
   double *q = nullptr, *rtil = nullptr, *qhat = nullptr, *res = nullptr, *tm = nullptr;
   double *dyacc = nullptr, *rhs = nullptr;
   double *r_alt = nullptr, *d_alt = nullptr;   // second buffers of the CG residual / direction
-  float* qf = nullptr;         // 2 x m: atomically accumulated CG products (FP32 streams)
+  double* qf = nullptr;        // 2 x kQCopies x m: atomically accumulated CG products (FP32 streams)
 
   // per-CTA partials of the column-tile kernels
   void* part = nullptr;
@@ -201,7 +203,7 @@ struct ColArgs {
   double* dnew;
   // CG with FP32 accumulation: add the row sums into qacc with atomics instead of writing
   // partials; the last CTA forms d^T q (d = dnew) and alpha = rho / d^T q in scw / flw.
-  float* qacc;
+  double* qacc;
   unsigned* cnt;
   double* scw;
   int* flw;
@@ -306,8 +308,8 @@ enum SymvMode { SYMV_PLAIN = 0, SYMV_CG_INIT = 1, SYMV_CG_STEP = 2, SYMV_F2 = 3 
 cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* rold,
                                 const double* q, const double* d, double* dy, double* rnew,
                                 double* z, double* sc, int* fl, double* bpart, unsigned* bcnt,
-                                cudaStream_t st, const float* qf = nullptr,
-                                float* qzero = nullptr);
+                                cudaStream_t st, const double* qf = nullptr,
+                                double* qzero = nullptr);
 cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, double* z,
                              double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
                              cudaStream_t st);

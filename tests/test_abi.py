@@ -51,7 +51,7 @@ def test_params_default_and_status_strings(lib):
 
     p = pkg.lp_params_default()
     assert p.tol == 1e-8 and p.sigma == 0.5 and p.sketch_s == 4 and p.cg_rel_tol == 1e-6
-    assert ctypes.sizeof(pkg.lp_params) == 72
+    assert ctypes.sizeof(pkg.lp_params) == 80
     from paper_2003_08072_gb300 import _binding
 
     assert _binding.status_str(0) == "LP_OK"
@@ -75,6 +75,10 @@ def test_argument_errors_need_no_device(lib):
         B.lp_create(4, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1, params=bad)
     bad = pkg.lp_params_default()
     bad.sketch_w = 18   # not a multiple of s = 4
+    with pytest.raises(pkg.LPError):
+        B.lp_create(4, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1, params=bad)
+    bad = pkg.lp_params_default()
+    bad.inner_solver = 2   # neither CG nor Richardson
     with pytest.raises(pkg.LPError):
         B.lp_create(4, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1, params=bad)
     with pytest.raises(pkg.LPError):
