@@ -184,57 +184,85 @@ __device__ __forceinline__ void df_tile_mul(const DFTile& A, const DFTile& B, fl
 
 // Factor and invert a diagonal block in double-float arithmetic: T (DF tile, SPD) is replaced
 // by its Cholesky factor L (lower triangle) in place, X receives L^{-1}; both are written to
-// global DF storage at offset off.  One thread takes each square root and reciprocal; the
-// trailing updates and the triangular inverse use all 256 threads.  A Schur pivot below 1e-14
-// of the original diagonal entry of Q (q0) counts as lost: returns false.
+// global DF storage at offset off.  The caller has loaded T and synchronised.  A Schur pivot
+// below 1e-14 of the original diagonal entry of Q (q0) counts as lost: returns false.
+//
+// The block is on the factorization's critical path (one per block step), so the elimination
+// is kept short: pivot p updates a_ij -= a_ip a_jp / a_pp (p < j <= i) with 1/a_pp read from
+// shared memory, and the thread that owns a_{p+1,p+1} forms its reciprocal as soon as it has
+// updated it, before the one barrier of the step.  Column p is never touched after step p, so
+// after the sweep the lower triangle holds the unscaled columns; square roots and the scaling
+// into L happen afterwards for all columns at once.  L^{-1} is then formed column by column:
+// the 8 threads of a column sit in one warp and read only their own column, so its rows are
+// ordered by warp barriers alone.
 __device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl, size_t off, int mp,
                            const double* q0, DFTile& X) {
-  __shared__ float inv_h[kNB], inv_l[kNB];
+  __shared__ float rp_h[kNB], rp_l[kNB];   // 1 / (Schur pivot p)
+  __shared__ float inv_h[kNB], inv_l[kNB]; // 1 / l_pp
   __shared__ int s_ok;
   const int tid = threadIdx.x;
-  if (tid == 0) s_ok = 1;
+  // a lost pivot is replaced by |q0| to keep the arithmetic finite; the flag aborts the solve
+  auto pivot_recip = [&](int p) {
+    float dh = T.h[p][p], dl = T.l[p][p];
+    if (!((double)dh + (double)dl > 1e-14 * q0[p]) || !isfinite(dh)) {
+      s_ok = 0;
+      dh = (float)fmax(fabs(q0[p]), 1e-30);
+      dl = 0.f;
+      T.h[p][p] = dh;
+      T.l[p][p] = dl;
+    }
+    df_recip(dh, dl, rp_h[p], rp_l[p]);
+  };
+  if (tid == 0) {
+    s_ok = 1;
+    pivot_recip(0);
+  }
+  __syncthreads();
   for (int p = 0; p < kNB; ++p) {
-    __syncthreads();
-    if (tid == 0) {
-      float dh = T.h[p][p], dl = T.l[p][p];
-      if (!((double)dh + (double)dl > 1e-14 * q0[p]) || !isfinite(dh)) {
-        s_ok = 0;
-        dh = (float)fmax(fabs(q0[p]), 1e-30);   // keep the arithmetic finite; the flag aborts
-        dl = 0.f;
-      }
-      float lh, ll, ih, il;
-      df_sqrt(dh, dl, lh, ll);
-      df_recip(lh, ll, ih, il);
-      T.h[p][p] = lh;
-      T.l[p][p] = ll;
-      inv_h[p] = ih;
-      inv_l[p] = il;
-    }
-    __syncthreads();
-    if (tid > p && tid < kNB) {
-      float h, l;
-      df_mul(T.h[tid][p], T.l[tid][p], inv_h[p], inv_l[p], h, l);
-      T.h[tid][p] = h;
-      T.l[tid][p] = l;
-    }
-    __syncthreads();
+    const float rh = rp_h[p], rl = rp_l[p];
+    bool own_next = false;
 #pragma unroll
     for (int k = 0; k < (kNB * kNB) / 256; ++k) {
       const int e = tid + 256 * k;
       const int i = e / kNB, j = e % kNB;
       if (j > p && j <= i) {
-        float h, l;
-        df_mul(T.h[i][p], T.l[i][p], T.h[j][p], T.l[j][p], h, l);
+        float th, tl, h, l;
+        df_mul(T.h[i][p], T.l[i][p], T.h[j][p], T.l[j][p], th, tl);
+        df_mul(th, tl, rh, rl, h, l);
         float a = T.h[i][j], b = T.l[i][j];
         df_add(a, b, -h, -l);
         T.h[i][j] = a;
         T.l[i][j] = b;
+        if (i == p + 1 && j == p + 1) own_next = true;
       }
+    }
+    if (own_next) pivot_recip(p + 1);
+    __syncthreads();
+  }
+  // l_pp = sqrt(a_pp), 1 / l_pp for every column at once, then l_ip = a_ip / l_pp
+  if (tid < kNB) {
+    float lh, ll;
+    df_sqrt(T.h[tid][tid], T.l[tid][tid], lh, ll);
+    df_recip(lh, ll, inv_h[tid], inv_l[tid]);
+    T.h[tid][tid] = lh;
+    T.l[tid][tid] = ll;
+  }
+  __syncthreads();
+  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, cc = e % kNB;
+    if (cc < r) {
+      float h, l;
+      df_mul(T.h[r][cc], T.l[r][cc], inv_h[cc], inv_l[cc], h, l);
+      T.h[r][cc] = h;
+      T.l[r][cc] = l;
+    } else if (cc > r) {
+      T.h[r][cc] = 0.f;
+      T.l[r][cc] = 0.f;
     }
   }
   __syncthreads();
   // X = L^{-1}, row by row: X_ij = -inv_ii sum_{j<=q<i} L_iq X_qj (j < i), X_ii = inv_ii;
-  // 8 threads per column share the sum and reduce with shuffles.
+  // the 8 threads of column j (one warp) share the sum and reduce with shuffles.
   const int j = tid >> 3, part = tid & 7;
   for (int i = 0; i < kNB; ++i) {
     float s = 0.f, c = 0.f;
@@ -256,13 +284,14 @@ __device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl
       X.h[i][j] = h;
       X.l[i][j] = l;
     }
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
   for (int e = tid; e < kNB * kNB; e += blockDim.x) {
     const int r = e / kNB, cc = e % kNB;
     const size_t a = off + (size_t)r * mp + cc;
-    Lh[a] = cc <= r ? T.h[r][cc] : 0.f;
-    Ll[a] = cc <= r ? T.l[r][cc] : 0.f;
+    Lh[a] = T.h[r][cc];
+    Ll[a] = T.l[r][cc];
     Xh[a] = X.h[r][cc];
     Xl[a] = X.l[r][cc];
   }
