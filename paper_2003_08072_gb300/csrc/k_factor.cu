@@ -187,56 +187,80 @@ __device__ __forceinline__ void df_tile_mul(const DFTile& A, const DFTile& B, fl
 // global DF storage at offset off.  The caller has loaded T and synchronised.  A Schur pivot
 // below 1e-14 of the original diagonal entry of Q (q0) counts as lost: returns false.
 //
-// The block is on the factorization's critical path (one per block step), so the elimination
-// is kept short: pivot p updates a_ij -= a_ip a_jp / a_pp (p < j <= i) with 1/a_pp read from
-// shared memory, and the thread that owns a_{p+1,p+1} forms its reciprocal as soon as it has
-// updated it, before the one barrier of the step.  Column p is never touched after step p, so
-// after the sweep the lower triangle holds the unscaled columns; square roots and the scaling
-// into L happen afterwards for all columns at once.  L^{-1} is then formed column by column:
-// the 8 threads of a column sit in one warp and read only their own column, so its rows are
-// ordered by warp barriers alone.
+// The block is on the factorization's critical path (one per block step), so its dependency
+// chains are kept short.  Pivot p updates a_ij -= a_ip a_jp / a_pp (p < j <= i): each thread
+// loads the inputs of its four elements before it stores any result (so the four chains
+// overlap), 1/a_pp comes from shared memory, and the thread that owns a_{p+1,p+1} forms its
+// reciprocal from the value it just computed, before the one barrier of the step.  Column p is
+// never touched after step p, so after the sweep the lower triangle holds the unscaled
+// columns; square roots and the scaling into L happen afterwards for all columns at once.
+// L^{-1} is formed column by column: the 8 threads of a column sit in one warp and read only
+// their own column, so its rows are ordered by warp barriers alone.
 __device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl, size_t off, int mp,
                            const double* q0, DFTile& X) {
   __shared__ float rp_h[kNB], rp_l[kNB];   // 1 / (Schur pivot p)
   __shared__ float inv_h[kNB], inv_l[kNB]; // 1 / l_pp
   __shared__ int s_ok;
   const int tid = threadIdx.x;
-  // a lost pivot is replaced by |q0| to keep the arithmetic finite; the flag aborts the solve
-  auto pivot_recip = [&](int p) {
-    float dh = T.h[p][p], dl = T.l[p][p];
-    if (!((double)dh + (double)dl > 1e-14 * q0[p]) || !isfinite(dh)) {
+  __shared__ float thr[kNB];                // lost-pivot threshold 1e-14 q0_p (FP32)
+  // a lost pivot is replaced by |q0| to keep the arithmetic finite; the flag aborts the solve.
+  // The test runs in FP32 (dh carries the pivot to 2^-24, far finer than 1e-14 q0 needs):
+  // FP64 latency on this GPU would otherwise sit on every step of the chain.
+  auto pivot_recip = [&](int p, float dh, float dl) {
+    if (!(dh > thr[p]) || !isfinite(dh)) {
       s_ok = 0;
-      dh = (float)fmax(fabs(q0[p]), 1e-30);
+      dh = fmaxf(thr[p] * 1e14f, 1e-30f);
       dl = 0.f;
       T.h[p][p] = dh;
       T.l[p][p] = dl;
     }
     df_recip(dh, dl, rp_h[p], rp_l[p]);
   };
+  if (tid < kNB) thr[tid] = (float)(1e-14 * fabs(q0[tid]));
+  __syncthreads();
   if (tid == 0) {
     s_ok = 1;
-    pivot_recip(0);
+    pivot_recip(0, T.h[0][0], T.l[0][0]);
   }
   __syncthreads();
+  constexpr int K = (kNB * kNB) / 256;   // elements per thread
   for (int p = 0; p < kNB; ++p) {
     const float rh = rp_h[p], rl = rp_l[p];
-    bool own_next = false;
+    float aih[K], ail[K], ajh[K], ajl[K], xh[K], xl[K];
+    bool act[K];
 #pragma unroll
-    for (int k = 0; k < (kNB * kNB) / 256; ++k) {
+    for (int k = 0; k < K; ++k) {
       const int e = tid + 256 * k;
       const int i = e / kNB, j = e % kNB;
-      if (j > p && j <= i) {
-        float th, tl, h, l;
-        df_mul(T.h[i][p], T.l[i][p], T.h[j][p], T.l[j][p], th, tl);
-        df_mul(th, tl, rh, rl, h, l);
-        float a = T.h[i][j], b = T.l[i][j];
-        df_add(a, b, -h, -l);
-        T.h[i][j] = a;
-        T.l[i][j] = b;
-        if (i == p + 1 && j == p + 1) own_next = true;
+      act[k] = j > p && j <= i;
+      if (act[k]) {
+        aih[k] = T.h[i][p];
+        ail[k] = T.l[i][p];
+        ajh[k] = T.h[j][p];
+        ajl[k] = T.l[j][p];
+        xh[k] = T.h[i][j];
+        xl[k] = T.l[i][j];
       }
     }
-    if (own_next) pivot_recip(p + 1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (act[k]) {
+        float th, tl, h, l;
+        df_mul(aih[k], ail[k], ajh[k], ajl[k], th, tl);
+        df_mul(th, tl, rh, rl, h, l);
+        df_add(xh[k], xl[k], -h, -l);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int e = tid + 256 * k;
+      const int i = e / kNB, j = e % kNB;
+      if (act[k]) {
+        T.h[i][j] = xh[k];
+        T.l[i][j] = xl[k];
+        if (i == p + 1 && j == p + 1) pivot_recip(p + 1, xh[k], xl[k]);
+      }
+    }
     __syncthreads();
   }
   // l_pp = sqrt(a_pp), 1 / l_pp for every column at once, then l_ip = a_ip / l_pp
