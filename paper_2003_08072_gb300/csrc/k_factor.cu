@@ -16,11 +16,22 @@ namespace lpk {
 constexpr int kGT = 64;   // Gram tile
 constexpr int kGK = 16;   // Gram k-chunk
 
+// G (FP64) -> hi + lo floats, once per factorization.  The split costs FP64 conversions, slow
+// on this GPU; done inside the tile kernel it was repeated for every tile pair an entry meets
+// (m / 64 + 1 times) and bounded the Gram product.
+__global__ void k_split_df(const double* __restrict__ G, size_t count, float* __restrict__ Gh,
+                           float* __restrict__ Gl) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    split_double(G[i], Gh[i], Gl[i]);
+}
+
 // One 64 x 64 lower tile of G G^T over a slice of the w columns, in double-float arithmetic on
-// the FP32 pipes: each FP64 entry of G is split into hi + lo floats when staged in shared
-// memory; hi*hi products are accumulated with TwoProduct/TwoSum, the cross terms plainly.
-__global__ void __launch_bounds__(256) k_gram_tile(const double* __restrict__ G, int ldg, int m, int w,
-                                                   int chunk, double* __restrict__ Qsplit,
+// the FP32 pipes from the hi + lo split of G; hi*hi products are accumulated with
+// TwoProduct/TwoSum, the cross terms plainly.
+__global__ void __launch_bounds__(256) k_gram_tile(const float* __restrict__ Gh,
+                                                   const float* __restrict__ Gl, int ldg, int m,
+                                                   int w, int chunk, double* __restrict__ Qsplit,
                                                    int ntiles) {
   __shared__ __align__(16) float Ah[kGK][kGT + 4];
   __shared__ __align__(16) float Al[kGK][kGT + 4];
@@ -44,8 +55,12 @@ __global__ void __launch_bounds__(256) k_gram_tile(const double* __restrict__ G,
       const int kk = idx >> 6, r = idx & 63;
       const int ra = ib * kGT + r, rb = jb * kGT + r;
       const bool kin = (k + kk) < k1;
-      split_double((kin && ra < m) ? G[(size_t)(k + kk) * ldg + ra] : 0.0, Ah[kk][r], Al[kk][r]);
-      split_double((kin && rb < m) ? G[(size_t)(k + kk) * ldg + rb] : 0.0, Bh[kk][r], Bl[kk][r]);
+      const bool va = kin && ra < m, vb = kin && rb < m;
+      const size_t ia = (size_t)(k + kk) * ldg + ra, ibb = (size_t)(k + kk) * ldg + rb;
+      Ah[kk][r] = va ? Gh[ia] : 0.f;
+      Al[kk][r] = va ? Gl[ia] : 0.f;
+      Bh[kk][r] = vb ? Gh[ibb] : 0.f;
+      Bl[kk][r] = vb ? Gl[ibb] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -112,14 +127,18 @@ int gram_split(int m, int w, int num_sms) {
   return split;
 }
 
-cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* Q, double* Qsplit,
-                        int split, cudaStream_t st) {
+cudaError_t launch_gram(const double* G, float* Gdf, int ldg, int m, int w, int mp, double* Q,
+                        double* Qsplit, int split, cudaStream_t st) {
   const int nt = mp / kGT;
   const int ntiles = nt * (nt + 1) / 2;
   int chunk = (w + split - 1) / split;
   chunk = (chunk + kGK - 1) / kGK * kGK;
+  const size_t count = (size_t)ldg * w;
+  float* Gh = Gdf;
+  float* Gl = Gdf + count;
+  { note_launch(); k_split_df<<<2048, 256, 0, st>>>(G, count, Gh, Gl); }
   dim3 grid(ntiles, split);
-  { note_launch(); k_gram_tile<<<grid, 256, 0, st>>>(G, ldg, m, w, chunk, Qsplit, ntiles); }
+  { note_launch(); k_gram_tile<<<grid, 256, 0, st>>>(Gh, Gl, ldg, m, w, chunk, Qsplit, ntiles); }
   { note_launch(); k_gram_finish<<<ntiles, 256, 0, st>>>(Qsplit, split, ntiles, m, mp, Q); }
   return cudaGetLastError();
 }

@@ -186,7 +186,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->vals);
   void* bufs[] = {c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
-                  c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G,
+                  c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
                   c->bcnt};
   for (void* p : bufs) dfree(p);
@@ -229,6 +229,7 @@ static lp_status alloc_workspace(lp_ctx* c) {
   LP_TRY(dalloc(&c->G, (size_t)c->ldg * c->w));
   LP_CU(cudaMemsetAsync(c->G, 0, (size_t)c->ldg * c->w * sizeof(double), c->st));
   LP_TRY(dalloc(&c->u, (size_t)c->w));
+  LP_TRY(dalloc(&c->Gdf, (size_t)2 * c->ldg * c->w));
   // factor
   c->mp = round_up(m, 64);
   LP_TRY(dalloc(&c->Q, (size_t)c->mp * c->mp));
@@ -769,7 +770,7 @@ static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
 // then only a preconditioner, and (A D W)^dagger is applied by PCG on Q itself.
 static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
   PhaseScope ps(c, LP_PH_FACTOR);
-  LP_CU(launch_gram(G, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
+  LP_CU(launch_gram(G, c->Gdf, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
   double eps = 0.0;
   for (;;) {
     LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
@@ -1191,7 +1192,7 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   b += 9 * 8 * dn + 4 * dn + 16 * 8 * dm;                                  // n- and m-vectors
   b += (double)std::max(coltile_max_grid(num_sms), csc_max_grid(num_sms)) * 2 * dm * 8;
   b += dn * s * (4 + 4 + 8) + 2.0 * kQCopies * dm * 8 + 3.0 * (w + 1) * 4; // sketch indices, q
-  b += (double)round_up(m, 2) * w * 8 + (double)w * 8;                     // G, u
+  b += (double)round_up(m, 2) * w * 16 + (double)w * 8;                    // G, its split, u
   b += 3.0 * mp * mp * 8;                                                  // Q, M, X
   b += (double)gram_split(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;
   b += (SC_COUNT + kMaxRedBlocks * 8) * 8.0 + FL_COUNT * 4 + 64;

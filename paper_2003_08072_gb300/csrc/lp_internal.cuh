@@ -128,6 +128,7 @@ struct lp_ctx {
   int32_t* list = nullptr;     // n*s entries: column | sign bit 31
   float2* coef = nullptr;      // n*s entries: sign d_i / sqrt(s) as a double-float pair
   double* G = nullptr;         // m x w column-major, leading dimension ldg (even)
+  float* Gdf = nullptr;        // G split into hi and lo floats (2 ldg w) for the Gram product
   int ldg = 0;
   double* u = nullptr;         // w
 
@@ -287,8 +288,9 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
                                      cudaStream_t st);
 
 // factor
-cudaError_t launch_gram(const double* G, int ldg, int m, int w, int mp, double* Q, double* Qsplit,
-                        int split, cudaStream_t st);
+// Q = G G^T (double-float, split along w); Gdf: 2 ldg w floats of work space (hi, lo of G)
+cudaError_t launch_gram(const double* G, float* Gdf, int ldg, int m, int w, int mp, double* Q,
+                        double* Qsplit, int split, cudaStream_t st);
 cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double eps,
                              const double* v, cudaStream_t st);
 cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
