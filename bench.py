@@ -42,11 +42,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["dense", "sparse", "scaled", "serving"],
+    ap.add_argument("--workload", choices=["dense", "sparse", "scaled", "serving", "svm"],
                     default="dense",
                     help="dense: Gaussian m x n; sparse: CSR with --nnz-per-col nonzeros per "
                          "column; scaled: dense with column scales 10^U(-3,3); serving: a "
-                         "Poisson stream of mixed dense/CSR LPs through the serving loop")
+                         "Poisson stream of mixed dense/CSR LPs through the serving loop; svm: "
+                         "the l1-SVM LP on synthetic separable data with a Table 1 shape")
+    ap.add_argument("--svm-shape", choices=["arcene", "dexter", "drivface", "gene_rna"],
+                    default="arcene")
     ap.add_argument("--requests", type=int, default=256, help="serving: stream length")
     ap.add_argument("--rate", type=str, default="2000",
                     help="serving: arrival rates in LP/s (comma separated, one run each)")
@@ -66,8 +69,13 @@ def parse_args():
     ap.add_argument("--cpu-sample-n", type=int, default=20_000)
     ap.add_argument("--cpu-sample-iters", type=int, default=4)
     args = ap.parse_args()
+    if args.workload == "svm":
+        import synth
+
+        pts, feats = synth.SVM_SHAPES[args.svm_shape]
+        args.m, args.n = pts, 2 * feats + 2 + pts
     defaults = {"dense": (1000, 200_000), "sparse": (5000, 2_000_000), "scaled": (2000, 500_000),
-                "serving": (512, 102_400)}
+                "serving": (512, 102_400), "svm": (args.m, args.n)}
     dm, dn = defaults[args.workload]
     args.m = args.m or dm
     args.n = args.n or dn
@@ -195,7 +203,18 @@ def kernel_sha1():
         return hashlib.sha1(f.read()).hexdigest()
 
 
+def metric_name(args):
+    if (args.workload, args.m, args.n, args.dtype) == ("dense", 1000, 200_000, "f32"):
+        return "IPM LPs/s (Algorithm 2 to tolerance, dense m=1000 n=200000 FP32 LP)"
+    return f"IPM LPs/s (Algorithm 2 to tolerance, {args.workload} m={args.m} n={args.n})"
+
+
 def workload_name(args):
+    if args.workload == "svm":
+        pts = args.m
+        return (f"l1-SVM LP ({args.svm_shape} shape of Table 1: {pts} points, "
+                f"{(args.n - 2 - pts) // 2} features; synthetic separable Gaussian data), "
+                f"m={args.m} n={args.n} A {args.dtype.upper()}, Algorithm 2 to scaled KKT 1e-8")
     if args.workload == "sparse":
         return (f"sparse LP m={args.m} n={args.n}, {args.nnz_per_col} nonzeros per column (CSR, "
                 f"FP32 values, int32 columns), feasible by construction, Algorithm 2 to scaled "
@@ -213,6 +232,8 @@ def make_lp(args):
     if args.workload == "sparse":
         return synth.sparse_lp(0, args.m, args.n, nnz_per_col=args.nnz_per_col)
     np_dt = np.float32 if args.dtype == "f32" else np.float64
+    if args.workload == "svm":
+        return synth.l1svm_lp(1, args.m, (args.n - 2 - args.m) // 2, dtype=np_dt)
     scale = (-3, 3) if args.workload == "scaled" else None
     return synth.dense_lp(0, args.m, args.n, dtype=np_dt, col_scale=scale)
 
@@ -229,6 +250,26 @@ def cpu_threads():
     return os.cpu_count()
 
 
+def sample_lp(args):
+    """The instance the oracle is timed on: the workload's generator with n_s columns (the whole
+    instance for the l1-SVM LPs, which are small).  Returns (lp, A as FP64, n_s)."""
+    import numpy as np
+
+    import synth
+
+    ns = min(args.cpu_sample_n, args.n)
+    np_dt = np.float32 if args.dtype == "f32" else np.float64
+    if args.workload == "svm":
+        lp = synth.l1svm_lp(1, args.m, (args.n - 2 - args.m) // 2, dtype=np_dt)
+        return lp, lp.A.astype(np.float64), args.n
+    if args.workload == "sparse":
+        lp = synth.sparse_lp(0, args.m, ns, nnz_per_col=args.nnz_per_col)
+        return lp, lp.to_scipy(), ns
+    lp = synth.dense_lp(0, args.m, ns, dtype=np_dt,
+                        col_scale=(-3, 3) if args.workload == "scaled" else None)
+    return lp, lp.A.astype(np.float64), ns
+
+
 def oracle_sample(args, iters_per_lp: float):
     """Times the FP64 oracle's Algorithm 2 for a few iterations on a column sample of the
     workload (same generator and m, n_s columns) and converts to LP/s of the full instance:
@@ -238,14 +279,7 @@ def oracle_sample(args, iters_per_lp: float):
     import synth
     from oracle import iipm
 
-    ns = min(args.cpu_sample_n, args.n)
-    if args.workload == "sparse":
-        lp = synth.sparse_lp(0, args.m, ns, nnz_per_col=args.nnz_per_col)
-        A = lp.to_scipy()
-    else:
-        lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64,
-                            col_scale=(-3, 3) if args.workload == "scaled" else None)
-        A = lp.A.astype(np.float64)
+    lp, A, ns = sample_lp(args)
     prm = iipm.Params(ipm_max_iter=args.cpu_sample_iters, sketch_s=args.sketch_s)
     t0 = time.perf_counter()
     r = iipm.ipm_solve(A, lp.b, lp.c, prm)
@@ -370,9 +404,7 @@ def run_ours(args, rank, world, local):
     cg_total = statistics.mean(i.cg_iters_total for i in infos)
     value = world * args.steps / t_max
     line = {
-        "metric": "IPM LPs/s (Algorithm 2 to tolerance, dense m=1000 n=200000 FP32 LP)"
-        if (args.workload, args.m, args.n, args.dtype) == ("dense", 1000, 200_000, "f32") else
-        f"IPM LPs/s (Algorithm 2 to tolerance, {args.workload} m={args.m} n={args.n})",
+        "metric": metric_name(args),
         "value": value,
         "unit": "LP/s",
         "n_gpus": world,
@@ -597,14 +629,7 @@ def oracle_iters_per_lp(args) -> float:
     import synth
     from oracle import iipm
 
-    ns = min(args.cpu_sample_n, args.n)
-    if args.workload == "sparse":
-        lp = synth.sparse_lp(0, args.m, ns, nnz_per_col=args.nnz_per_col)
-        A = lp.to_scipy()
-    else:
-        lp = synth.dense_lp(0, args.m, ns, dtype=np.float32 if args.dtype == "f32" else np.float64,
-                            col_scale=(-3, 3) if args.workload == "scaled" else None)
-        A = lp.A.astype(np.float64)
+    lp, A, ns = sample_lp(args)
     r = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(), variant="exact")
     return float(r.iters)
 
@@ -625,7 +650,7 @@ def run_reference(args, rank, world):
     value = statistics.mean(vals)
     return {
         "impl": "reference",
-        "metric": "IPM LPs/s (Algorithm 2 to tolerance, dense m=1000 n=200000 FP32 LP)",
+        "metric": metric_name(args),
         "value": value, "unit": "LP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -198,3 +198,34 @@ def poisson_arrivals(count: int, rate: float, seed: int = 5) -> np.ndarray:
     """Arrival times (seconds from 0) of a Poisson stream of the given rate."""
     rng = np.random.default_rng([seed, 99])
     return np.cumsum(rng.exponential(1.0 / rate, count))
+
+
+# Shapes (training points, features) of the l1-SVM data sets of the paper's Table 1.
+SVM_SHAPES = {"arcene": (100, 10_000), "dexter": (300, 20_000), "drivface": (606, 6_400),
+              "gene_rna": (801, 20_531)}
+
+
+def l1svm_lp(seed: int, points: int, features: int, dtype=np.float64) -> DenseLP:
+    """Standard-form LP of an l1-regularised SVM on synthetic separable data.
+
+    Data: x_i ~ N(0, I) in R^features, labels y_i = sign(x_i^T w* + b*) for a random w*, b*
+    (separable, so the LP is feasible).  LP (points rows): variables
+    [w+ (features), w- (features), b+, b-, xi (points)] >= 0,
+      y_i (x_i^T (w+ - w-) + b+ - b-) - xi_i = 1,
+    cost 1 on w+, w-, b+, b- (||w||_1 + |b|) and 0 on the surplus xi.  The offset is priced
+    like the weights so that the optimal face stays bounded.
+    x0, y0, s0 are None (the IPM starts from x = s = 1, y = 0).
+    """
+    rng = np.random.default_rng([seed, 11])
+    X = rng.standard_normal((points, features))
+    wstar = rng.standard_normal(features)
+    bstar = rng.standard_normal()
+    y = np.sign(X @ wstar + bstar)
+    y[y == 0] = 1.0
+    YX = y[:, None] * X
+    A = np.concatenate([YX, -YX, y[:, None], -y[:, None], -np.eye(points)], axis=1)
+    At = np.ascontiguousarray(A.T.astype(dtype))
+    n = A.shape[1]
+    c = np.concatenate([np.ones(2 * features + 2), np.zeros(points)])
+    b = np.ones(points)
+    return DenseLP(At=At, b=b, c=c, x0=None, y0=None, s0=None)

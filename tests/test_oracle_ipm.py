@@ -377,3 +377,26 @@ def test_planted_mistakes_are_caught(monkeypatch):
     Wu_bad = iipm.apply_W(u_bad, it["sol"]["bucket"], it["sol"]["sign"])
     v_bad = np.sqrt(x * sv) * Wu_bad
     assert np.linalg.norm(A @ (v_bad / sv) - rtil) > 1e-3 * np.linalg.norm(rtil)
+
+
+def test_l1svm_lp_matches_highs_and_separates():
+    """The l1-SVM LP (App. D.1 formulation on synthetic separable data, Table 1's problem class):
+    the oracle's optimum equals HiGHS's, and the (w, b) it returns separates the training points
+    with margin 1 up to the tolerance."""
+    from scipy.optimize import linprog
+
+    pts, feats = 20, 200
+    lp = synth.l1svm_lp(0, pts, feats)
+    A = lp.A.astype(np.float64)
+    hi = linprog(lp.c, A_eq=A, b_eq=lp.b, bounds=(0, None), method="highs")
+    assert hi.status == 0
+    for variant in ("sketch", "exact"):
+        r = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(), variant=variant)
+        assert r.converged and r.kkt <= 1e-8
+        assert abs(r.obj - hi.fun) <= 1e-6 * abs(hi.fun)
+    w = r.x[:feats] - r.x[feats:2 * feats]
+    b = r.x[2 * feats] - r.x[2 * feats + 1]
+    YX = A[:, :feats]                       # rows y_i x_i^T
+    y = A[:, 2 * feats]                     # labels
+    margins = YX @ w + y * b
+    assert margins.min() >= 1 - 1e-6
