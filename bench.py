@@ -50,6 +50,9 @@ def parse_args():
                          "the l1-SVM LP on synthetic separable data with a Table 1 shape")
     ap.add_argument("--svm-shape", choices=["arcene", "dexter", "drivface", "gene_rna"],
                     default="arcene")
+    ap.add_argument("--sweep", action="store_true",
+                    help="svm: sweep sketch width w and relative CG tolerance (Fig. 2) instead "
+                         "of timing one configuration")
     ap.add_argument("--requests", type=int, default=256, help="serving: stream length")
     ap.add_argument("--rate", type=str, default="2000",
                     help="serving: arrival rates in LP/s (comma separated, one run each)")
@@ -619,6 +622,63 @@ def run_serving(args, rank, world, local):
     }
 
 
+# --------------------------------------------------------------------------- (w, tolCG) sweep
+
+def run_sweep(args, rank, world, local):
+    """Outer (IPM) and inner (CG) iterations against the sketch width w and the relative CG
+    tolerance tolCG (the paper's Fig. 2 study), with the relative rule alone deciding CG's stop,
+    and the condition numbers of Table 1 at the final iterate: kappa(A D^2 A^T) and the
+    preconditioned kappa(Q^-1/2 A D^2 A^T Q^-1/2) from the same sketch (FP64, host)."""
+    import numpy as np
+    import torch
+
+    import paper_2003_08072_gb300 as pkg
+    from paper_2003_08072_gb300 import _binding as B
+
+    if rank != 0:
+        return None
+    pkg.load()
+    torch.cuda.set_device(local)
+    lp = make_lp(args)
+    A = lp.A.astype(np.float64)
+    rows = []
+    for wm in (2, 4, 8, 16):
+        for tol in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+            prm = pkg.lp_params_default()
+            prm.sketch_w = (wm * args.m + prm.sketch_s - 1) // prm.sketch_s * prm.sketch_s
+            prm.cg_rel_tol = tol
+            prm.cg_theory_rule = 0
+            ctx = B.lp_create(args.m, args.n, B.LP_DENSE_COLMAJOR,
+                              B.LP_F32 if args.dtype == "f32" else B.LP_F64, lp.At, None, None, 0,
+                              lp.b, lp.c, prm, None)
+            x, y, s = np.empty(args.n), np.empty(args.m), np.empty(args.n)
+            t0 = time.perf_counter()
+            info = B.lp_ipm_solve(ctx, x, y, s, check=False)
+            secs = time.perf_counter() - t0
+            row = {"w": f"{wm}m", "tolCG": tol, "status": info.status, "outer": info.ipm_iters,
+                   "inner": info.cg_iters_total, "inner_per_outer": info.cg_iters_total /
+                   max(info.ipm_iters, 1), "ms": 1e3 * secs,
+                   "kkt": max(info.rp_rel, info.rd_rel, info.gap_rel)}
+            if tol == 1e-6 and info.status == 0:
+                d2 = x / s
+                K = A @ (d2[:, None] * A.T)
+                G = np.empty((prm.sketch_w, args.m))
+                Gt = torch.empty(prm.sketch_w, args.m, dtype=torch.float64, device="cuda")
+                B.lp_sketch(ctx, torch.from_numpy(np.sqrt(d2)).cuda(), info.ipm_iters - 1, Gt)
+                G = Gt.cpu().numpy().T
+                lam, V = np.linalg.eigh(G @ G.T)
+                Qmh = (V / np.sqrt(lam)) @ V.T
+                ev = np.linalg.eigvalsh(Qmh @ K @ Qmh)
+                evk = np.linalg.eigvalsh(K)
+                row["kappa_standard"] = float(evk[-1] / evk[0])
+                row["kappa_preconditioned"] = float(ev[-1] / ev[0])
+            B.lp_destroy(ctx)
+            rows.append(row)
+    return {"metric": "outer / inner iterations against sketch width and tolCG (Fig. 2 study)",
+            "value": None, "unit": "iterations", "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic", "config": {"workload": workload_name(args)}, "sweep": rows}
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def oracle_iters_per_lp(args) -> float:
@@ -669,6 +729,8 @@ def main():
         line = run_reference(args, rank, world)
     elif args.workload == "serving":
         line = run_serving(args, rank, world, local)
+    elif args.workload == "svm" and args.sweep:
+        line = run_sweep(args, rank, world, local)
     else:
         line = run_ours(args, rank, world, local)
     if rank == 0 and line is not None:
