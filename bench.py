@@ -30,8 +30,8 @@ if ROOT not in sys.path:
 
 # DRAM bytes of one CG product launch from an ncu capture of the same kernel source
 # (k_cgprod.cu at the recorded hash); reported only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha1": "fd110b3818d8a954ef953b094e23f38c81dd437a",
-               "bytes_per_launch": 804.05e6,
+NCU_TRAFFIC = {"source_sha1": "17ef797053cfa0a86cda223fd6d4ce62827ca631",
+               "bytes_per_launch": 804.09e6,
                "case": "dense m=1000 n=200000 FP32, ncu --set full (profiles/k_cgprod_cg_product_"
                        "dense_m1000_n200000_f32.md)"}
 

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
         double qi = 0.0;
 #pragma unroll
         for (int k = 0; k < kQCopies; ++k) qi += __ldcg(&a.qacc[(size_t)k * a.m + i]);
+        a.qsum[i] = qi;
         dq[0] += a.dnew[i] * qi;
       }
       block_sum<1>(dq);

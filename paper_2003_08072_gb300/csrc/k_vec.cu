@@ -163,7 +163,7 @@ struct SymvArgs {
   const double* q;
   const double* d;
   double* dy;
-  const double* qf;    // q accumulated in kQCopies atomic copies (instead of q)
+  const double* qf;    // the product's atomic q copies (q itself holds their sum)
   double* qzero;       // zeroed by CTA 0 for the next CG product
 };
 
@@ -181,15 +181,8 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
     double v = 0.0;
     if (i < a.m) {
       if (a.rold) {
-        double qi;
-        if (a.qf) {
-          double qs = 0.0;
-#pragma unroll
-          for (int k = 0; k < kQCopies; ++k) qs += a.qf[(size_t)k * a.m + i];
-          qi = qs;
-        } else {
-          qi = a.q[i];
-        }
+        // with atomic copies the product's last CTA has already summed them into q
+        const double qi = a.q[i];
         v = fma(-al, qi, a.rold[i]);
         if (blockIdx.x == 0) {
           const_cast<double*>(a.r)[i] = v;

@@ -561,6 +561,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     a.flw = c->fl;
     if (qacc && !acc64) {
       a.qacc = qacc;
+      a.qsum = out;
       a.cnt = c->bcnt + 1;
       a.scw = c->sc;
     } else {

@@ -205,6 +205,7 @@ struct ColArgs {
   // CG with FP32 accumulation: add the row sums into qacc with atomics instead of writing
   // partials; the last CTA forms d^T q (d = dnew) and alpha = rho / d^T q in scw / flw.
   double* qacc;
+  double* qsum;        // the last CTA also writes q = sum of the qacc copies here
   unsigned* cnt;
   double* scw;
   int* flw;
