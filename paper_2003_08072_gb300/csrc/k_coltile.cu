@@ -14,6 +14,10 @@
 // a coalesced 128-bit streaming load.  A CTA walks column tiles of TILE columns; the TILE
 // partial dots of a warp are combined by a transposing shuffle reduction, then across warps
 // through a double-buffered shared array (one __syncthreads per tile).
+//
+// Used for FP64 A (FP64 accumulation), the FP64 residual pass, the allocation-free entry point,
+// and any shape the shared-memory staged CG product (k_cgprod.cu) does not cover; FP32 A with
+// FP64-class accumulation goes to the double-float pass (k_coltile_df.cu).
 #include <algorithm>
 
 #include "dev_util.cuh"
