@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--stream", choices=["same", "f32", "bf16", "f16"], default="same")
     ap.add_argument("--sketch-s", type=int, default=4)
+    ap.add_argument("--sketch", choices=["sparse", "gaussian"], default="sparse",
+                    help="sparse sign sketch with --sketch-s nonzeros per row, or Gaussian")
     ap.add_argument("--cg-batch", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -314,6 +316,7 @@ def run_ours(args, rank, world, local):
     lp = make_lp(args)
     prm = pkg.lp_params_default()
     prm.sketch_s = args.sketch_s
+    prm.sketch_kind = 1 if args.sketch == "gaussian" else 0
     prm.cg_batch = args.cg_batch
     sparse = args.workload == "sparse"
     sd = (args.dtype if not sparse else "f32") if args.stream == "same" else args.stream
@@ -423,7 +426,8 @@ def run_ours(args, rank, world, local):
             "workload": workload_name(args),
             "m": args.m, "n": args.n, "a_dtype": "f32" if sparse else args.dtype,
             "stream_dtype": sd,
-            "sketch": f"sparse sign s={args.sketch_s}, w=4m", "cg_rel_tol": prm.cg_rel_tol,
+            "sketch": (f"sparse sign s={args.sketch_s}, w=4m" if args.sketch == "sparse" else
+                       "Gaussian, w=4m"), "cg_rel_tol": prm.cg_rel_tol,
             "tol": prm.tol, "sigma": prm.sigma, "gamma": prm.gamma,
             "l2": "inputs larger than L2 (A is %.0f MB)" % (a_bytes / 1e6),
             "parallelism": f"replicas x{world}",

@@ -58,6 +58,8 @@ typedef enum { LP_F64 = 0, LP_F32 = 1, LP_BF16 = 2, LP_F16 = 3 } lp_dtype;
 
 typedef enum { LP_INNER_CG = 0, LP_INNER_RICHARDSON = 1 } lp_inner_solver;
 
+typedef enum { LP_SKETCH_SPARSE = 0, LP_SKETCH_GAUSSIAN = 1 } lp_sketch_kind;
+
 /* Parameters of Algorithms 1 and 2.  Defaults from lp_params_default(). */
 typedef struct {
   double tol;            /* stop when ||r_p||/(1+||b||), ||r_d||/(1+||c||), n mu/(1+|c^T x|) <= tol (1e-8) */
@@ -83,6 +85,10 @@ typedef struct {
                             rule; it converges only when ||I - Q^{-1/2} A D^2 A^T Q^{-1/2}|| < 1, i.e.
                             for a sketch much wider than 4m, and a diverging run ends the solve with
                             LP_ERR_NOT_CONVERGED (0) */
+  int32_t sketch_kind;   /* LP_SKETCH_SPARSE (0): sketch_s nonzeros +-1/sqrt(s) per row of W (Sec. 2);
+                            LP_SKETCH_GAUSSIAN (1): W with N(0, 1/w) entries (Sec. 5, the sketch of the
+                            experiments, Sec. 6), dense A only; forming A D W costs 2 m n w, meant for
+                            the small LPs of the experiments (0) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */

@@ -73,3 +73,28 @@ def sketch_indices(seed: int, k: int, n: int, s: int, w: int):
               + lemire_reduce(h >> np.uint64(32), width).astype(np.int64))
     sign = np.where((h & np.uint64(1)) == 1, -1.0, 1.0)
     return bucket, sign
+
+
+def gaussian_W(seed: int, k: int, n: int, w: int, rows=None) -> np.ndarray:
+    """Dense Gaussian sketching matrix W (n x w) of iteration k, entries ~ N(0, 1/w).
+
+    The Gaussian sketch of the paper's experiments (Sec. 6) and of Sec. 5, generated from the
+    same per-iteration key: for entry (i, b), with t = i*w + b,
+        h1 = splitmix64(key_k ^ 2t),  h2 = splitmix64(key_k ^ (2t + 1)),
+        u1 = ((h1 >> 40) + 1) 2^-24 in (0, 1],  u2 = (h2 >> 40) 2^-24 in [0, 1),
+        z  = sqrt(-2 ln u1) cos(2 pi u2)      (Box & Muller, Ann. Math. Stat. 1958),
+        W[i, b] = z / sqrt(w).
+    24-bit uniforms are exact in FP32, so both sides start from identical u1, u2.
+    ``rows`` restricts the output to those row indices (default: all n).
+    """
+    key = iteration_key(seed, k)
+    i = (np.arange(n, dtype=np.uint64) if rows is None else np.asarray(rows, dtype=np.uint64))[:, None]
+    b = np.arange(w, dtype=np.uint64)[None, :]
+    with np.errstate(over="ignore"):
+        t = i * np.uint64(w) + b
+        h1 = splitmix64(key ^ (np.uint64(2) * t))
+        h2 = splitmix64(key ^ (np.uint64(2) * t + np.uint64(1)))
+    u1 = ((h1 >> np.uint64(40)).astype(np.float64) + 1.0) * 2.0**-24
+    u2 = (h2 >> np.uint64(40)).astype(np.float64) * 2.0**-24
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return z / np.sqrt(w)

@@ -31,7 +31,7 @@ from typing import Callable, Optional
 import numpy as np
 import scipy.linalg as sla
 
-from .hashing import sketch_indices
+from .hashing import gaussian_W, sketch_indices
 
 
 @dataclasses.dataclass
@@ -48,6 +48,7 @@ class Params:
     refine_max: int = 6         # steps of the FP64 refinement of Q^{-1} r~ (Sec. 4, Eq. compv)
     cg_theory_rule: bool = True # also stop only once ||f|| <= gamma sigma sqrt(mu)/(4 sqrt(n)) (Sec. 4)
     inner: str = "cg"           # "cg" (Alg. 1 step 3) or "richardson" (App. A)
+    sketch_kind: str = "sparse" # "sparse" (s nonzeros per row) or "gaussian" (Sec. 5, Sec. 6)
 
 
 # --------------------------------------------------------------------------
@@ -444,8 +445,13 @@ def normal_solve_sketch(A, x, s, p, k, prm: Params):
     w = prm.sketch_w or 4 * m
     d2 = x / s
     d = np.sqrt(d2)
-    bucket, sign = sketch_indices(prm.seed, k, n, prm.sketch_s, w)
-    G = sketch_ADW(A, d, bucket, sign, w)
+    if prm.sketch_kind == "gaussian":
+        Wg = gaussian_W(prm.seed, k, n, w)
+        G = sketch_ADW_given_W(A, d, Wg)
+        bucket = sign = None
+    else:
+        bucket, sign = sketch_indices(prm.seed, k, n, prm.sketch_s, w)
+        G = sketch_ADW(A, d, bucket, sign, w)
     R = factor_R(G)
     mv = lambda v: normal_matvec(A, d2, v)
     if prm.inner == "richardson":
@@ -456,7 +462,7 @@ def normal_solve_sketch(A, x, s, p, k, prm: Params):
                  abs_tol=cg_abs_threshold(x, s, prm))
     rtil = mv(cg.dy) - p
     u, qhat, steps = correction_u(G, R, rtil, prm.refine_max)
-    Wu = apply_W(u, bucket, sign)
+    Wu = Wg @ u if prm.sketch_kind == "gaussian" else apply_W(u, bucket, sign)
     return dict(dy=cg.dy, cg=cg, G=G, R=R, rtil=rtil, u=u, Wu=Wu, qhat=qhat,
                 refine_steps=steps, bucket=bucket, sign=sign, w=w)
 

@@ -19,6 +19,7 @@ LP_DENSE_COLMAJOR, LP_DENSE_ROWMAJOR, LP_CSR = 0, 1, 2
 LP_F64, LP_F32, LP_BF16, LP_F16 = 0, 1, 2, 3
 
 LP_INNER_CG, LP_INNER_RICHARDSON = 0, 1
+LP_SKETCH_SPARSE, LP_SKETCH_GAUSSIAN = 0, 1
 DTYPE_CODES = {"f64": LP_F64, "f32": LP_F32, "bf16": LP_BF16, "f16": LP_F16}
 
 
@@ -38,6 +39,7 @@ class lp_params(ctypes.Structure):
         ("stream_dtype", ctypes.c_int),
         ("cg_batch", ctypes.c_int32),
         ("inner_solver", ctypes.c_int32),
+        ("sketch_kind", ctypes.c_int32),
     ]
 
 

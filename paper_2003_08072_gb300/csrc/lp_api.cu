@@ -80,6 +80,7 @@ lp_status lp_params_default(lp_params* p) {
   p->stream_dtype = LP_F64;
   p->cg_batch = 4;
   p->inner_solver = LP_INNER_CG;
+  p->sketch_kind = LP_SKETCH_SPARSE;
   return LP_OK;
 }
 
@@ -94,6 +95,8 @@ static lp_status check_params(const lp_params& p, int m) {
   if (p.sketch_s < 1 || p.sketch_w < 0) return fail(LP_ERR_ARG, "invalid sketch size");
   if (p.inner_solver != LP_INNER_CG && p.inner_solver != LP_INNER_RICHARDSON)
     return fail(LP_ERR_ARG, "inner_solver must be LP_INNER_CG or LP_INNER_RICHARDSON");
+  if (p.sketch_kind != LP_SKETCH_SPARSE && p.sketch_kind != LP_SKETCH_GAUSSIAN)
+    return fail(LP_ERR_ARG, "sketch_kind must be LP_SKETCH_SPARSE or LP_SKETCH_GAUSSIAN");
   const int w = p.sketch_w ? p.sketch_w : 4 * m;
   if (w % p.sketch_s != 0) return fail(LP_ERR_ARG, "sketch_w must be a multiple of sketch_s");
   if (w < m) return fail(LP_ERR_ARG, "sketch_w must be >= m");
@@ -364,6 +367,8 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
   if (!A_vals || !b || !cvec) return fail(LP_ERR_ARG, "lp_create: NULL A, b or c");
   if (a_dtype != LP_F64 && a_dtype != LP_F32)
     return fail(LP_ERR_ARG, "lp_create: A must be LP_F64 or LP_F32");
+  if (layout == LP_CSR && prm && prm->sketch_kind == LP_SKETCH_GAUSSIAN)
+    return fail(LP_ERR_ARG, "lp_create: the Gaussian sketch needs a dense A");
   if (layout == LP_CSR && (!indptr || !indices || nnz < 0))
     return fail(LP_ERR_ARG, "lp_create: CSR needs indptr, indices and nnz");
   if (layout != LP_CSR && layout != LP_DENSE_COLMAJOR && layout != LP_DENSE_ROWMAJOR)
@@ -517,6 +522,8 @@ extern "C" lp_status lp_set_params(lp_ctx* c, const lp_params* prm) {
   const int w = prm->sketch_w ? prm->sketch_w : 4 * c->m;
   if (w != c->w || prm->sketch_s != c->ss)
     return fail(LP_ERR_ARG, "lp_set_params: sketch size is fixed at lp_create");
+  if (c->sparse && prm->sketch_kind == LP_SKETCH_GAUSSIAN)
+    return fail(LP_ERR_ARG, "lp_set_params: the Gaussian sketch needs a dense A");
   lp_dtype sd = prm->stream_dtype == LP_F64 ? c->a_dtype : prm->stream_dtype;
   if (!c->sparse && sd != c->s_dtype && !(sd == LP_F64 && c->a_dtype == LP_F32))
     return fail(LP_ERR_ARG, "lp_set_params: stream dtype is fixed at lp_create");
@@ -751,6 +758,11 @@ static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, cons
 // Alg. 1 step 1 / Alg. 2 step (a): G = A D W(seed, k).
 static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
   PhaseScope ps(c, LP_PH_SKETCH);
+  if (c->prm.sketch_kind == LP_SKETCH_GAUSSIAN) {
+    LP_CU(launch_sketch_gauss(c->a_dtype, c->A, c->lda, c->m, c->n, c->w, c->prm.seed, k, d, G,
+                              c->ldg, c->st));
+    return LP_OK;
+  }
   LP_CU(cudaMemsetAsync(c->cnt, 0, (c->w + 1) * sizeof(int32_t), c->st));
   LP_CU(launch_sketch_hash(c->prm.seed, k, c->n, c->ss, c->w, c->hb, c->cnt, nullptr, nullptr, c->st));
   LP_CU(launch_sketch_scan(c->cnt, c->w, c->start, c->cursor, c->st));
@@ -1026,7 +1038,13 @@ extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, in
     inf.refine_steps = so.refine;
     inf.f_norm = so.f_norm;
     inf.f_target = so.f_target;
-    st = run_step(c, c->x, c->y, c->s, c->rd, c->dyacc, c->t, nullptr, eta, mu0, c->dx, c->ds);
+    const double* wu_given = nullptr;
+    if (c->prm.sketch_kind == LP_SKETCH_GAUSSIAN) {
+      // the fused update gathers W u from the sparse W's buckets; the Gaussian W needs W u first
+      LP_CU(launch_apply_W_gauss(c->prm.seed, k, c->n, c->w, c->u, c->wu, c->st));
+      wu_given = c->wu;
+    }
+    st = run_step(c, c->x, c->y, c->s, c->rd, c->dyacc, c->t, wu_given, eta, mu0, c->dx, c->ds);
     if (st != LP_OK) {
       result = st;
       break;
@@ -1074,7 +1092,10 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
   if (rtil) LP_CU(cudaMemcpyAsync(rtil, c->rtil, c->m * sizeof(double), cudaMemcpyDefault, c->st));
   if (u) LP_CU(cudaMemcpyAsync(u, c->u, c->w * sizeof(double), cudaMemcpyDefault, c->st));
   if (Atdy) LP_CU(cudaMemcpyAsync(Atdy, c->t, c->n * sizeof(double), cudaMemcpyDefault, c->st));
-  if (Wu) LP_CU(launch_apply_W(c->hb, c->ss, c->u, c->n, Wu, c->st));
+  if (Wu && c->prm.sketch_kind == LP_SKETCH_GAUSSIAN)
+    LP_CU(launch_apply_W_gauss(c->prm.seed, k, c->n, c->w, c->u, Wu, c->st));
+  else if (Wu)
+    LP_CU(launch_apply_W(c->hb, c->ss, c->u, c->n, Wu, c->st));
   LP_CU(cudaStreamSynchronize(c->st));
   if (info) {
     lp_info inf{};

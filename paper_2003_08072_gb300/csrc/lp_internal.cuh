@@ -348,6 +348,12 @@ int gram_split(int m, int w, int num_sms);
 // conversions
 cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, int m, int64_t n,
                                  void* dst, lp_dtype ddt, int ldd, cudaStream_t st);
+// Gaussian sketch G = A D W (dense A, FP32 or FP64) and W u, W from (seed, k) (k_gauss.cu)
+cudaError_t launch_sketch_gauss(lp_dtype ta, const void* A, int64_t lda, int m, int64_t n, int w,
+                                uint64_t seed, int k, const double* d, double* G, int ldg,
+                                cudaStream_t st);
+cudaError_t launch_apply_W_gauss(uint64_t seed, int k, int64_t n, int w, const double* u, double* wu,
+                                 cudaStream_t st);
 // Raises (never lowers) a kernel's dynamic shared-memory limit to at least `bytes`.
 cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
 cudaError_t launch_convert_colscaled(const void* src, lp_dtype sdt, int lda, int m, int64_t n,

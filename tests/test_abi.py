@@ -81,6 +81,10 @@ def test_argument_errors_need_no_device(lib):
     bad.inner_solver = 2   # neither CG nor Richardson
     with pytest.raises(pkg.LPError):
         B.lp_create(4, 10, B.LP_DENSE_COLMAJOR, B.LP_F64, 1, None, None, 0, 1, 1, params=bad)
+    bad = pkg.lp_params_default()
+    bad.sketch_kind = B.LP_SKETCH_GAUSSIAN   # needs a dense A
+    with pytest.raises(pkg.LPError):
+        B.lp_create(4, 10, B.LP_CSR, B.LP_F64, 1, 1, 1, 4, 1, 1, params=bad)
     with pytest.raises(pkg.LPError):
         B.lp_sketch_indices(0, 0, 10, 3, 16, 1, 1)   # w % s != 0
 

@@ -80,3 +80,51 @@ def test_sketch_preserves_norms_in_expectation():
             W = iipm.sketch_W_dense(b, sg, 64)
             ratios.append(np.sum((W.T @ z) ** 2) / np.sum(z ** 2))
         assert abs(np.mean(ratios) - 1.0) < 0.05
+
+
+# ------------------------------------------------------------------ Gaussian sketch generator
+
+def test_gaussian_W_moments_and_normality():
+    """W's entries times sqrt(w) are N(0, 1): moments within 5 sigma of their sampling error,
+    and a Kolmogorov-Smirnov test against the normal CDF."""
+    from scipy import stats
+
+    n, w = 5000, 400
+    z = (hashing.gaussian_W(0, 3, n, w) * np.sqrt(w)).ravel()
+    N = z.size
+    assert abs(z.mean()) <= 5 / np.sqrt(N)
+    assert abs(z.var() - 1.0) <= 5 * np.sqrt(2.0 / N)
+    assert abs(np.mean(z**4) - 3.0) <= 5 * np.sqrt(96.0 / N)
+    assert stats.kstest(z[:200_000], "norm").pvalue > 1e-3
+
+
+def test_gaussian_W_is_a_function_of_seed_and_iteration_only():
+    a = hashing.gaussian_W(7, 2, 300, 64)
+    assert np.array_equal(a, hashing.gaussian_W(7, 2, 300, 64))
+    assert np.array_equal(a[[5, 17]], hashing.gaussian_W(7, 2, 300, 64, rows=[5, 17]))
+    assert not np.allclose(a, hashing.gaussian_W(7, 3, 300, 64))
+    assert not np.allclose(a, hashing.gaussian_W(8, 2, 300, 64))
+    # neighbouring entries are uncorrelated
+    z = hashing.gaussian_W(1, 0, 4000, 100).ravel()
+    assert abs(np.corrcoef(z[:-1], z[1:])[0, 1]) <= 5 / np.sqrt(z.size)
+
+
+def test_gaussian_W_is_an_isometry_in_expectation():
+    """W W^T -> I_n (entries N(0, 1/w)): for w >> n the deviation is O(sqrt(n/w))."""
+    n, w = 40, 40_000
+    W = hashing.gaussian_W(0, 1, n, w)
+    dev = np.linalg.norm(W @ W.T - np.eye(n), 2)
+    assert dev <= 3 * (2 * np.sqrt(n / w) + n / w)
+
+
+def test_gaussian_sketch_spectrum_within_marchenko_pastur_edges():
+    """For the Gaussian sketch, eig(V^T W W^T V) (V: right singular vectors of A D, m of them)
+    lie close to the Marchenko-Pastur support [(1 - sqrt(m/w))^2, (1 + sqrt(m/w))^2]."""
+    m, n, w = 30, 3000, 600
+    rng = np.random.default_rng(4)
+    AD = rng.standard_normal((m, n)) * np.exp(rng.uniform(-2, 2, n))[None, :]
+    _, _, Vt = np.linalg.svd(AD, full_matrices=False)
+    W = hashing.gaussian_W(0, 5, n, w)
+    ev = np.linalg.eigvalsh(Vt @ W @ W.T @ Vt.T)
+    r = np.sqrt(m / w)
+    assert ev.min() >= (1 - r) ** 2 - 0.1 and ev.max() <= (1 + r) ** 2 + 0.1

@@ -400,3 +400,18 @@ def test_l1svm_lp_matches_highs_and_separates():
     y = A[:, 2 * feats]                     # labels
     margins = YX @ w + y * b
     assert margins.min() >= 1 - 1e-6
+
+
+def test_ipm_with_gaussian_sketch_matches_highs():
+    """Algorithm 2 with the Gaussian sketch (Sec. 5, the paper's experiments) on the m=40,
+    n=2000 LP: HiGHS's optimum, iterations within one of the exact-direction variant."""
+    from scipy.optimize import linprog
+
+    lp = synth.dense_lp(0, 40, 2000)
+    A = lp.A.astype(np.float64)
+    hi = linprog(lp.c, A_eq=A, b_eq=lp.b, bounds=(0, None), method="highs")
+    ex = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(), variant="exact")
+    g = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(sketch_kind="gaussian"))
+    assert g.converged and g.kkt <= 1e-8
+    assert abs(g.obj - hi.fun) <= 1e-6 * abs(hi.fun)
+    assert abs(g.iters - ex.iters) <= 1
