@@ -69,7 +69,8 @@ typedef struct {
   int32_t cg_max_iter;   /* CG iteration cap per solve (500) */
   int32_t ipm_max_iter;  /* IPM iteration cap (200) */
   int32_t refine_max;    /* FP64 refinement steps for Q^{-1} r~ and for a low-precision dy (6) */
-  int32_t sketch_s;      /* nonzeros per row of W: 1 = CountSketch, 4 = sparse sign (4) */
+  int32_t sketch_s;      /* nonzeros per row of W: 1 = CountSketch, 4 = sparse sign (4); unused by the
+                            Gaussian sketch */
   int32_t sketch_w;      /* sketch width w; 0 = 4m.  Must be a multiple of sketch_s */
   int32_t cg_theory_rule;/* 1: CG also stops only once ||f|| <= gamma sigma sqrt(mu)/(4 sqrt(n)) (Sec. 4) (1) */
   uint64_t seed;         /* W for IPM iteration k is a function of (seed, k) only (0) */
@@ -134,8 +135,12 @@ const char* lp_last_error(void);
  * The context owns all device memory it allocates: the matrix in the layout
  * the kernels stream (column-major with 16-byte aligned columns, or CSC),
  * a low-precision copy when prm->stream_dtype asks for one, and the
- * workspaces.  Errors: LP_ERR_ARG (sizes, NULL, non-finite entries, dtype),
- * LP_ERR_OOM, LP_ERR_CUDA.  Synchronous.
+ * workspaces (lp_footprint_bytes bounds the total).  The memory comes from the
+ * device's default stream-ordered pool (cudaMallocAsync on `stream`); the
+ * library raises that pool's release threshold so that memory freed by
+ * lp_destroy stays cached in the process for the next context.
+ * Errors: LP_ERR_ARG (sizes, NULL, non-finite entries, dtype, the Gaussian
+ * sketch with CSR), LP_ERR_OOM, LP_ERR_CUDA.  Synchronous.
  */
 lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout layout, lp_dtype a_dtype,
                     const void* A_vals, const int64_t* indptr, const int32_t* indices, int64_t nnz,
