@@ -7,7 +7,7 @@ triangular solve) serve as single steps; nothing is blocked, fused or
 reordered beyond what the cited passage states.  ``A`` is an (m, n) float64
 array or a scipy.sparse matrix; vectors are float64.
 
-Readings of passages the paper leaves open (all listed in the design doc):
+Readings of passages the paper leaves open:
   * r_p lives in R^m and r_d in R^n (Sec. 1 swaps the dimensions).
   * Q^{-1/2} is used through any factor R with R^T R = Q (Alg. 1, step 2):
     PCG with preconditioner M = Q produces the same dy iterates as CG on
