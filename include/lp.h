@@ -77,8 +77,8 @@ typedef struct {
   lp_dtype stream_dtype; /* dtype A is streamed in by the CG matvec; LP_F64 keeps the input dtype (LP_F64).
                             Dense LP_BF16 / LP_F16 copies hold column j scaled by a power of two 2^-e_j
                             (max |entry| in [0.5, 1)), the scales folded into D^2.  A copy below the
-                            input precision is corrected by FP64 refinement; when a refinement round
-                            fails to halve ||f|| (or refine_max rounds pass) the solve streams the
+                            input precision is corrected by FP64 refinement; when a refinement pass
+                            fails to halve ||f|| (or refine_max passes run) the solve streams the
                             input-precision copy from then on (lp_info.stream_switch_iter). */
   int32_t cg_batch;      /* CG iterations enqueued between host checks of the stop flag (4) */
   int32_t inner_solver;  /* LP_INNER_CG (0): Alg. 1 step 3; LP_INNER_RICHARDSON (1): the preconditioned

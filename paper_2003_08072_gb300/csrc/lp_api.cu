@@ -889,7 +889,7 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
     abs_thr = c->prm.gamma * c->prm.sigma * sqrt(mu) / (4.0 * sqrt((double)c->n));
   bool lowprec = c->s_dtype != LP_F64;   // CG products accumulate in FP32
   double rho0 = 0.0, target2 = 0.0, f2_prev = INFINITY, contraction = 0.0;
-  int total_it = 0, outer = 0, rounds = 0;
+  int total_it = 0, outer = 0, passes = 0;
   for (;;) {
     int it = 0;
     double r0 = 0.0, rl = 0.0;
@@ -902,8 +902,8 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
     } else {
       // refinement: solve (A D^2 A^T) delta = -r~ and add it to dy.  The residual of
       // dy + delta is the residual of this solve, so it stops at the solve's own target, or
-      // once its own residual is below what the streamed operator can deliver in one round
-      // (the contraction of the previous round times the current ||f||): solving the
+      // once its own residual is below what the streamed operator can deliver in one pass
+      // (the contraction of the previous pass times the current ||f||): solving the
       // rounded system further would not shrink the true residual.
       LP_CU(launch_vec_ops(VOP_NEG, c->rhs, c->rtil, nullptr, m, nullptr, c->st));
       const double thr = std::max(0.5 * sqrt(target2), 0.5 * contraction * sqrt(f2_prev));
@@ -927,25 +927,25 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
     if (!lowprec || f2 <= 4.0 * target2) break;
     // Refinement converges when the streamed operator is close enough to A D^2 A^T in the
     // preconditioned norm; rounding A to 16 bits perturbs it by ~2^-9 relative per entry,
-    // which a badly conditioned A D stretches past 1.  A round that fails to halve ||f||
-    // (or the round cap) switches the solve to the master copy for the remaining IPM
+    // which a badly conditioned A D stretches past 1.  A refinement pass that fails to halve
+    // ||f|| (or the pass cap) switches the solve to the master copy for the remaining IPM
     // iterations; without a copy to switch to, the cap ends the refinement.
-    // contraction of this round: ||f|| after it over ||f|| before it (round 0 starts from
-    // ||f^(0)|| = sqrt(rho0)); 1/8 or worse after the first solve also means many rounds
-    contraction = sqrt(f2 / (rounds == 0 ? std::max(rho0, 1e-300) : f2_prev));
-    const bool stalled = (rounds == 0 && contraction > 0.125) || (rounds >= 1 && f2 > 0.25 * f2_prev);
-    if (stalled || rounds >= c->prm.refine_max) {
+    // contraction of this pass: ||f|| after it over ||f|| before it (pass 0 starts from
+    // ||f^(0)|| = sqrt(rho0)); 1/8 or worse after the first solve also means many passes
+    contraction = sqrt(f2 / (passes == 0 ? std::max(rho0, 1e-300) : f2_prev));
+    const bool stalled = (passes == 0 && contraction > 0.125) || (passes >= 1 && f2 > 0.25 * f2_prev);
+    if (stalled || passes >= c->prm.refine_max) {
       if (!stream_switch(c, k)) {
-        if (rounds >= c->prm.refine_max) break;
+        if (passes >= c->prm.refine_max) break;
       } else {
         lowprec = c->s_dtype != LP_F64;
-        rounds = 0;
-        contraction = 0.0;   // the master copy's rounds solve to the target
+        passes = 0;
+        contraction = 0.0;   // the master copy's passes solve to the target
       }
     }
     f2_prev = f2;
     ++outer;
-    ++rounds;
+    ++passes;
   }
   so->cg_iters = total_it;
   // u = (A D W)^dagger r~ = (A D W)^T q with Q q = r~ (Eq. compv, full row rank): PCG on
