@@ -53,6 +53,10 @@ def parse_args():
     ap.add_argument("--sweep", action="store_true",
                     help="svm: sweep sketch width w and relative CG tolerance (Fig. 2) instead "
                          "of timing one configuration")
+    ap.add_argument("--sketch-study", action="store_true",
+                    help="dense or svm: compare CountSketch (s=1), sparse sign s=2/4/8 and the "
+                         "Gaussian sketch at w = 4m, and the factor routes, instead of timing "
+                         "one configuration")
     ap.add_argument("--requests", type=int, default=256, help="serving: stream length")
     ap.add_argument("--rate", type=str, default="2000",
                     help="serving: arrival rates in LP/s (comma separated, one run each)")
@@ -683,6 +687,97 @@ def run_sweep(args, rank, world, local):
             "data": "synthetic", "config": {"workload": workload_name(args)}, "sweep": rows}
 
 
+# --------------------------------------------------------------------------- sketch study
+
+def preconditioned_kappa(K, L):
+    """kappa of L^T K L (the spectrum of M K for the preconditioner M = L L^T), or None when
+    the result is not positive definite."""
+    import numpy as np
+
+    ev = np.linalg.eigvalsh(L.T @ K @ L)
+    return float(ev[-1] / ev[0]) if ev[0] > 0 else None
+
+
+def run_sketch_study(args, rank, world, local):
+    """CountSketch (s = 1) against the sparse sign sketch with s = 2, 4, 8 nonzeros per row and
+    the Gaussian sketch (dense A), all at w = 4m (rounded up to a multiple of s) with the default CG rules: outer and inner
+    iterations and time per LP, and at the final iterate (W of the last IPM iteration):
+    kappa(Q) for Q = G G^T, the preconditioned kappa with the exact Q^-1/2 (eigendecomposition,
+    the paper's SVD route), with the GPU's preconditioner M (Gram product and Cholesky inverse
+    in double-float) and with a host QR factor of G^T (FP64), and ||M Q - I||_2 for the last
+    two.  All host arithmetic is FP64."""
+    import numpy as np
+    import scipy.linalg as sl
+    import torch
+
+    import paper_2003_08072_gb300 as pkg
+    from paper_2003_08072_gb300 import _binding as B
+
+    if rank != 0:
+        return None
+    pkg.load()
+    torch.cuda.set_device(local)
+    lp = make_lp(args)
+    A = lp.A.astype(np.float64)
+    m, n = args.m, args.n
+    variants = [("CountSketch s=1", B.LP_SKETCH_SPARSE, 1), ("sparse sign s=2", B.LP_SKETCH_SPARSE, 2),
+                ("sparse sign s=4", B.LP_SKETCH_SPARSE, 4), ("sparse sign s=8", B.LP_SKETCH_SPARSE, 8)]
+    if 8.0 * m * m * n <= 3e11:   # the Gaussian A D W costs 2 m n w = 8 m^2 n flops per IPM iteration
+        variants.append(("Gaussian", B.LP_SKETCH_GAUSSIAN, 4))
+    rows = []
+    for name, kind, ns in variants:
+        prm = pkg.lp_params_default()
+        prm.sketch_kind = kind
+        prm.sketch_s = ns
+        prm.sketch_w = (4 * m + ns - 1) // ns * ns      # w = 4m, rounded up to a multiple of s
+        ctx = B.lp_create(m, n, B.LP_DENSE_COLMAJOR, B.LP_F32 if args.dtype == "f32" else B.LP_F64,
+                          lp.At, None, None, 0, lp.b, lp.c, prm, None)
+        x, y, s = np.empty(n), np.empty(m), np.empty(n)
+        t0 = time.perf_counter()
+        info = B.lp_ipm_solve(ctx, x, y, s, check=False)
+        secs = time.perf_counter() - t0
+        row = {"sketch": name, "status": info.status, "outer": info.ipm_iters,
+               "inner": info.cg_iters_total,
+               "inner_per_outer": info.cg_iters_total / max(info.ipm_iters, 1),
+               "ms": 1e3 * secs, "kkt": max(info.rp_rel, info.rd_rel, info.gap_rel),
+               "obj": info.obj}
+        if info.status == 0:
+            w = prm.sketch_w
+            d2 = x / s
+            K = A @ (d2[:, None] * A.T)
+            Gt = torch.empty(w, m, dtype=torch.float64, device="cuda")
+            B.lp_sketch(ctx, torch.from_numpy(np.sqrt(d2)).cuda(), info.ipm_iters - 1, Gt)
+            G = Gt.cpu().numpy().T
+            Q = G @ G.T
+            lam, V = np.linalg.eigh(Q)
+            row["kappa_Q"] = float(lam[-1] / lam[0]) if lam[0] > 0 else None
+            row["kappa_standard"] = float(np.linalg.cond(K))
+            row["kappa_pre_exact"] = (preconditioned_kappa(K, V / np.sqrt(lam))
+                                      if lam[0] > 0 else None)
+            R = np.linalg.qr(G.T, mode="r")
+            X = sl.solve_triangular(R, np.eye(m))
+            row["kappa_pre_qr"] = preconditioned_kappa(K, X)
+            row["qr_MQ_minus_I"] = float(np.linalg.norm(X @ (X.T @ Q) - np.eye(m), 2))
+            Qd = torch.empty(m, m, dtype=torch.float64, device="cuda")
+            Mi = torch.empty(m, m, dtype=torch.float64, device="cuda")
+            try:
+                B.lp_factor(ctx, Gt, Qd, Mi)
+                M = Mi.cpu().numpy()
+                M = 0.5 * (M + M.T)
+                row["gpu_MQ_minus_I"] = float(np.linalg.norm(M @ Q - np.eye(m), 2))
+                try:
+                    row["kappa_pre_gpu"] = preconditioned_kappa(K, np.linalg.cholesky(M))
+                except np.linalg.LinAlgError:
+                    row["kappa_pre_gpu"] = None
+            except pkg.LPError as e:
+                row["gpu_factor"] = f"status {e.status} (the IPM's own factor shifts Q here)"
+        B.lp_destroy(ctx)
+        rows.append(row)
+    return {"metric": "iterations and condition numbers against the sketch kind (w = 4m)",
+            "value": None, "unit": "iterations", "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic", "config": {"workload": workload_name(args)}, "study": rows}
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def oracle_iters_per_lp(args) -> float:
@@ -735,6 +830,8 @@ def main():
         line = run_serving(args, rank, world, local)
     elif args.workload == "svm" and args.sweep:
         line = run_sweep(args, rank, world, local)
+    elif args.sketch_study and args.workload in ("dense", "svm"):
+        line = run_sketch_study(args, rank, world, local)
     else:
         line = run_ours(args, rank, world, local)
     if rank == 0 and line is not None:

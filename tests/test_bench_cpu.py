@@ -61,3 +61,19 @@ def test_reference_arm_line_on_a_small_instance():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_preconditioned_kappa():
+    """The sketch study's kappa of M K with M = L L^T: the identity preconditioner gives
+    cond(K), the exact K^-1/2 gives 1, and an indefinite product is reported as None."""
+    import numpy as np
+
+    import bench
+
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((30, 30))
+    K = F @ F.T + 0.1 * np.eye(30)
+    assert bench.preconditioned_kappa(K, np.eye(30)) == pytest.approx(np.linalg.cond(K), rel=1e-8)
+    lam, V = np.linalg.eigh(K)
+    assert bench.preconditioned_kappa(K, V / np.sqrt(lam)) == pytest.approx(1.0, abs=1e-10)
+    assert bench.preconditioned_kappa(-K, np.eye(30)) is None
