@@ -53,7 +53,8 @@ def solve_dense(lp, prm):
 
 
 @pytest.mark.parametrize("dt,sd,s", [("f64", "f64", 4), ("f64", "f64", 1), ("f32", "f32", 4),
-                                     ("f64", "f32", 4), ("f64", "bf16", 4)])
+                                     ("f64", "f32", 4), ("f64", "bf16", 4), ("f64", "f64", 2),
+                                     ("f32", "f32", 8)])
 def test_ipm_dense_config1(dt, sd, s):
     import paper_2003_08072_gb300 as pkg
 

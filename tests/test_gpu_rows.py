@@ -118,17 +118,18 @@ def test_residuals_and_rhs(case):
 # ------------------------------------------------------------------ a2: sketch A D W
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("s", [1, 4])
+@pytest.mark.parametrize("s", [1, 2, 4, 8])
 def test_sketch_matches_oracle(case, s):
-    solver, A, lp, prm = make(*case, sketch_s=s)
     m, n = case[1], case[2]
+    w = (4 * m + s - 1) // s * s        # 4m rounded up to a multiple of s
+    solver, A, lp, prm = make(*case, sketch_s=s, sketch_w=w)
     x, y, sv = synth.iterate_point(5, m, n, spread=3.0)
     d = np.sqrt(x / sv)
     for k in (0, 9):
         G = N(solver.sketch(T(d), k))
-        b, sg = hashing.sketch_indices(prm.seed, k, n, s, 4 * m)
-        OG = iipm.sketch_ADW(A, d, b, sg, 4 * m)
-        scale = np.abs(A).max() * np.abs(d).max() * max(1, n * s // (4 * m)) ** 0.5 * 4
+        b, sg = hashing.sketch_indices(prm.seed, k, n, s, w)
+        OG = iipm.sketch_ADW(A, d, b, sg, w)
+        scale = np.abs(A).max() * np.abs(d).max() * max(1, n * s // w) ** 0.5 * 4
         assert G.shape == OG.shape
         assert close(G, OG, 1e-12, scale)
 
