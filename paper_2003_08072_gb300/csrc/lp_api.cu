@@ -3,7 +3,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <memory>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -377,7 +379,9 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
   if (prm) p = *prm; else lp_params_default(&p);
   LP_TRY(check_params(p, m));
 
-  lp_ctx* c = new lp_ctx();
+  // no C++ exception may leave an extern "C" entry point: host allocations are nothrow
+  lp_ctx* c = new (std::nothrow) lp_ctx();
+  if (!c) return fail(LP_ERR_OOM, "lp_create: host allocation failed");
   c->m = m;
   c->n = n;
   c->prm = p;
@@ -470,15 +474,20 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
     if (e == cudaSuccess) e = cudaMemcpyAsync(ix, indices, nnz * sizeof(int32_t), cudaMemcpyDefault, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(vv, A_vals, nnz * es, cudaMemcpyDefault, c->st);
     // validate the structure on the host copy of indptr (small) and the indices on device
-    std::vector<int64_t> hip(m + 1);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hip.data(), ip, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
+    std::unique_ptr<int64_t[]> hip(new (std::nothrow) int64_t[(size_t)m + 1]);
+    if (!hip) {
+      dfree(ip); dfree(ix); dfree(vv); dfree(cur);
+      return bail(fail(LP_ERR_OOM, "lp_create: host allocation failed"));
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hip.get(), ip, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     bool ok = (e == cudaSuccess) && hip[0] == 0 && hip[m] == nnz;
     for (int i = 0; ok && i < m; ++i) ok = hip[i] <= hip[i + 1];
     if (ok) {
       // column ids in range: reuse the finiteness flag through a tiny check on host copy
-      std::vector<int32_t> hix(nnz);
-      if (cudaMemcpyAsync(hix.data(), ix, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st) !=
+      std::unique_ptr<int32_t[]> hix(new (std::nothrow) int32_t[nnz > 0 ? (size_t)nnz : 1]);
+      if (!hix ||
+          cudaMemcpyAsync(hix.get(), ix, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st) !=
               cudaSuccess ||
           cudaStreamSynchronize(c->st) != cudaSuccess)
         ok = false;
@@ -992,9 +1001,11 @@ extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, in
     LP_CU(cudaMemcpyAsync(c->y, y, m * sizeof(double), cudaMemcpyDefault, c->st));
     LP_CU(cudaMemcpyAsync(c->s, s, n * sizeof(double), cudaMemcpyDefault, c->st));
   } else {
-    std::vector<double> ones(std::max<int64_t>(n, 1), 1.0);
-    LP_CU(cudaMemcpyAsync(c->x, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    LP_CU(cudaMemcpyAsync(c->s, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    std::unique_ptr<double[]> ones(new (std::nothrow) double[n > 0 ? (size_t)n : 1]);
+    if (!ones) return fail(LP_ERR_OOM, "lp_ipm_solve: host allocation failed");
+    std::fill(ones.get(), ones.get() + n, 1.0);
+    LP_CU(cudaMemcpyAsync(c->x, ones.get(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    LP_CU(cudaMemcpyAsync(c->s, ones.get(), n * sizeof(double), cudaMemcpyHostToDevice, c->st));
     LP_CU(cudaMemsetAsync(c->y, 0, m * sizeof(double), c->st));
     LP_CU(cudaStreamSynchronize(c->st));
   }

@@ -14,7 +14,9 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -74,9 +76,17 @@ namespace {
 
 void solve_one(lp_server* sv, Request* r, cudaStream_t st) {
   lp_ctx* ctx = nullptr;
-  r->x.assign(r->n, 0.0);
-  r->y.assign(r->m, 0.0);
-  r->s.assign(r->n, 0.0);
+  // no exception may end a worker thread: a failed host allocation fails the request
+  try {
+    r->x.assign(r->n, 0.0);
+    r->y.assign(r->m, 0.0);
+    r->s.assign(r->n, 0.0);
+  } catch (const std::bad_alloc&) {
+    r->status = LP_ERR_OOM;
+    r->info.status = LP_ERR_OOM;
+    r->error = "lp_server: host allocation for the result failed";
+    return;
+  }
   lp_status status = lp_create(&ctx, r->m, r->n, r->layout, r->a_dtype, r->A.data(),
                                r->layout == LP_CSR ? r->indptr.data() : nullptr,
                                r->layout == LP_CSR ? r->indices.data() : nullptr, r->nnz,
@@ -149,7 +159,11 @@ lp_status lp_server_create(lp_server** out, uint64_t mem_budget_bytes, int32_t m
     lp_set_error("lp_server_create: need 1 <= max_live <= 256 and a nonzero budget");
     return LP_ERR_ARG;
   }
-  auto sv = std::make_unique<lp_server>();
+  std::unique_ptr<lp_server> sv(new (std::nothrow) lp_server());
+  if (!sv) {
+    lp_set_error("lp_server_create: host allocation failed");
+    return LP_ERR_OOM;
+  }
   if (prm) sv->prm = *prm; else lp_params_default(&sv->prm);
   if (cudaGetDevice(&sv->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->dev) !=
@@ -160,7 +174,15 @@ lp_status lp_server_create(lp_server** out, uint64_t mem_budget_bytes, int32_t m
   }
   sv->budget = mem_budget_bytes;
   sv->max_live = max_live;
-  for (int i = 0; i < max_live; ++i) sv->workers.emplace_back(worker_main, sv.get());
+  try {
+    sv->workers.reserve(max_live);
+    for (int i = 0; i < max_live; ++i) sv->workers.emplace_back(worker_main, sv.get());
+  } catch (const std::exception&) {
+    // could not start every worker (std::system_error or std::bad_alloc): stop the ones running
+    lp_server_destroy(sv.release());
+    lp_set_error("lp_server_create: could not start the worker threads");
+    return LP_ERR_OOM;
+  }
   *out = sv.release();
   return LP_OK;
 }
@@ -179,7 +201,11 @@ lp_status lp_server_submit(lp_server* sv, int32_t m, int64_t n, lp_layout layout
     lp_set_error("lp_server_submit: bad sizes, dtype or CSR arrays");
     return LP_ERR_ARG;
   }
-  auto r = std::make_unique<Request>();
+  std::unique_ptr<Request> r(new (std::nothrow) Request());
+  if (!r) {
+    lp_set_error("lp_server_submit: host allocation failed");
+    return LP_ERR_OOM;
+  }
   r->m = m;
   r->n = n;
   r->layout = layout;
@@ -188,13 +214,18 @@ lp_status lp_server_submit(lp_server* sv, int32_t m, int64_t n, lp_layout layout
   const size_t es = dtype_bytes(a_dtype);
   const size_t count = layout == LP_CSR ? (size_t)nnz : (size_t)m * (size_t)n;
   const auto* src = reinterpret_cast<const unsigned char*>(A_vals);
-  r->A.assign(src, src + count * es);
-  if (layout == LP_CSR) {
-    r->indptr.assign(indptr, indptr + m + 1);
-    r->indices.assign(indices, indices + nnz);
+  try {
+    r->A.assign(src, src + count * es);
+    if (layout == LP_CSR) {
+      r->indptr.assign(indptr, indptr + m + 1);
+      r->indices.assign(indices, indices + nnz);
+    }
+    r->b.assign(b, b + m);
+    r->c.assign(c, c + n);
+  } catch (const std::bad_alloc&) {
+    lp_set_error("lp_server_submit: host allocation for the request copy failed");
+    return LP_ERR_OOM;
   }
-  r->b.assign(b, b + m);
-  r->c.assign(c, c + n);
   r->footprint = lp_footprint_bytes(m, n, layout, a_dtype, r->nnz, &sv->prm, sv->num_sms);
   if (r->footprint > sv->budget) {
     lp_set_error("lp_server_submit: the instance alone exceeds the admission budget");
@@ -204,9 +235,16 @@ lp_status lp_server_submit(lp_server* sv, int32_t m, int64_t n, lp_layout layout
     std::lock_guard<std::mutex> lk(sv->mu);
     r->ticket = sv->next_ticket++;
     r->t_submit = now_s();
-    *ticket = r->ticket;
-    sv->queue.push_back(r.get());
-    sv->all.emplace(r->ticket, std::move(r));
+    Request* raw = r.get();
+    try {
+      sv->all.emplace(raw->ticket, std::move(r));
+      sv->queue.push_back(raw);
+    } catch (const std::bad_alloc&) {
+      sv->all.erase(raw->ticket);
+      lp_set_error("lp_server_submit: host allocation failed");
+      return LP_ERR_OOM;
+    }
+    *ticket = raw->ticket;
     ++sv->submitted;
   }
   sv->cv_work.notify_one();
