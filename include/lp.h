@@ -169,6 +169,38 @@ lp_status lp_ipm_solve(lp_ctx* ctx, double* x, double* y, double* s, int32_t sta
                        lp_info* info);
 
 /*
+ * Checkpoint / resume of Algorithm 2.  Besides the iterate (x, y, s), a run carries its
+ * iteration counter k (iteration k draws W = W(seed, k), step (a)) and the references of the
+ * neighbourhood N(gamma) fixed at its start point (Sec. 4: ||r^k|| / ||r^0|| <= mu_k / mu_0),
+ * plus the iteration at which the CG products switched to the master copy of A.  With these a
+ * solve stopped at the iteration cap (LP_ERR_NOT_CONVERGED) or saved to storage continues as
+ * if it had not stopped: same W stream, same neighbourhood, same stream dtype.
+ */
+typedef struct {
+  int32_t k;                  /* IPM iterations taken since the start point */
+  int32_t stream_switch_iter; /* iteration of the switch to the master copy of A; -1 if none */
+  double r0;                  /* ||(r_p, r_d)|| at the start point */
+  double mu0;                 /* x^T s / n at the start point */
+} lp_ipm_state;
+
+/* State at the end of the last lp_ipm_solve / lp_ipm_resume on ctx (k = 0 and r0 = mu0 = 0
+ * before the first).  LP_ERR_ARG for NULL arguments. */
+lp_status lp_ipm_get_state(lp_ctx* ctx, lp_ipm_state* state);
+
+/*
+ * lp_ipm_resume -- lp_ipm_solve continued from a checkpoint (any context holding the same
+ * A, b, c and seed, e.g. a new process).
+ *   x, y, s : host or device, n, m, n float64; on entry the iterate saved with *state
+ *             (x, s > 0), on exit the last iterate.
+ *   state   : from lp_ipm_get_state after the run being continued; k >= 0, r0 >= 0, mu0 > 0.
+ * ipm_max_iter caps the total count k, so raise it (lp_set_params) to continue a run that
+ * stopped at the cap.  info->ipm_iters is the total count; the CG counts are this call's.
+ * Errors as lp_ipm_solve, plus LP_ERR_ARG for a state out of range.  Synchronous.
+ */
+lp_status lp_ipm_resume(lp_ctx* ctx, double* x, double* y, double* s, const lp_ipm_state* state,
+                        lp_info* info);
+
+/*
  * lp_normal_solve -- Algorithm 1 plus the correction of Eq. compv for one iterate.
  *   x, s    : device, n float64, strictly positive; D^2 = X S^{-1} (Sec. 1).
  *   p       : device, m float64 right-hand side.

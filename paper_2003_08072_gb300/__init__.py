@@ -14,7 +14,8 @@ from __future__ import annotations
 
 from ._binding import (DTYPE_CODES, LP_CSR, LP_DENSE_COLMAJOR, LP_DENSE_ROWMAJOR, LP_BF16,
                        LP_F16, LP_F32, LP_F64, LPError, lp_create, lp_destroy, lp_factor,
-                       lp_info, lp_ipm_solve, lp_normal_matvec, lp_normal_solve, lp_params,
+                       lp_info, lp_ipm_get_state, lp_ipm_resume, lp_ipm_solve,
+                       lp_ipm_state, lp_normal_matvec, lp_normal_solve, lp_params,
                        lp_params_default, lp_profile, lp_profile_enable, lp_profile_read,
                        lp_residuals, lp_set_params, lp_sketch,
                        lp_sketch_indices, lp_step, load, lp_footprint_bytes)
@@ -27,5 +28,5 @@ __all__ = [
     "lp_sketch_indices", "lp_sketch", "lp_factor", "lp_normal_matvec", "lp_step",
     "LP_DENSE_COLMAJOR", "LP_DENSE_ROWMAJOR", "LP_CSR", "LP_F64", "LP_F32", "LP_BF16", "LP_F16",
     "DTYPE_CODES", "lp_profile", "lp_profile_enable", "lp_profile_read", "LPServer",
-    "lp_footprint_bytes",
+    "lp_footprint_bytes", "lp_ipm_state", "lp_ipm_get_state", "lp_ipm_resume",
 ]

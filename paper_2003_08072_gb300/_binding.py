@@ -68,6 +68,17 @@ class lp_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lp_ipm_state(ctypes.Structure):
+    """Algorithm 2's state beyond the iterate (include/lp.h): iteration counter, stream switch,
+    and the start point's residual norm and mu."""
+    _fields_ = [
+        ("k", ctypes.c_int32),
+        ("stream_switch_iter", ctypes.c_int32),
+        ("r0", ctypes.c_double),
+        ("mu0", ctypes.c_double),
+    ]
+
+
 class lp_profile(ctypes.Structure):
     _fields_ = [
         ("phase_ms", ctypes.c_double * 8),
@@ -122,6 +133,9 @@ _SIGNATURES = {
     "lp_destroy": (None, [_VP]),
     "lp_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(lp_params)]),
     "lp_ipm_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, ctypes.POINTER(lp_info)]),
+    "lp_ipm_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(lp_ipm_state)]),
+    "lp_ipm_resume": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(lp_ipm_state),
+                                     ctypes.POINTER(lp_info)]),
     "lp_normal_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP,
                                        ctypes.POINTER(lp_info)]),
     "lp_residuals": (ctypes.c_int, [_VP, _VP, _VP, _VP, _D, _VP, _VP, _VP, ctypes.POINTER(_D)]),
@@ -225,6 +239,20 @@ def lp_set_params(ctx, params: lp_params):
 def lp_ipm_solve(ctx, x, y, s, start_given=False, check=True) -> lp_info:
     info = lp_info()
     st = load().lp_ipm_solve(ctx, _p(x), _p(y), _p(s), 1 if start_given else 0, ctypes.byref(info))
+    if check and st not in (LP_OK,):
+        raise LPError(st, last_error())
+    return info
+
+
+def lp_ipm_get_state(ctx) -> lp_ipm_state:
+    st = lp_ipm_state()
+    _check(load().lp_ipm_get_state(ctx, ctypes.byref(st)))
+    return st
+
+
+def lp_ipm_resume(ctx, x, y, s, state: lp_ipm_state, check=True) -> lp_info:
+    info = lp_info()
+    st = load().lp_ipm_resume(ctx, _p(x), _p(y), _p(s), ctypes.byref(state), ctypes.byref(info))
     if check and st not in (LP_OK,):
         raise LPError(st, last_error())
     return info

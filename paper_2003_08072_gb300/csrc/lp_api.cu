@@ -989,13 +989,14 @@ static lp_status run_step(lp_ctx* c, double* x, double* y, double* s, const doub
 // Entry points
 // ------------------------------------------------------------------------------------------
 
-extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, int32_t start_given,
-                                  lp_info* info) {
-  if (!c || !x || !y || !s) return fail(LP_ERR_ARG, "lp_ipm_solve: NULL argument");
+// Algorithm 2 from the start point (resume == nullptr) or continued from a checkpoint.
+static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_given,
+                         const lp_ipm_state* resume, lp_info* info) {
   stream_reset(c);
   const int m = c->m;
   const int64_t n = c->n;
   lp_info inf{};
+  if (resume && resume->stream_switch_iter >= 0) stream_switch(c, resume->stream_switch_iter);
   if (start_given) {
     LP_CU(cudaMemcpyAsync(c->x, x, n * sizeof(double), cudaMemcpyDefault, c->st));
     LP_CU(cudaMemcpyAsync(c->y, y, m * sizeof(double), cudaMemcpyDefault, c->st));
@@ -1012,10 +1013,11 @@ extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, in
   const double sigma = c->prm.sigma;
   LP_TRY(run_residuals(c, c->x, c->y, c->s, sigma, c->rp, c->rd, c->p));
   LP_TRY(sync_scalars(c));
-  const double mu0 = c->sc_h[SC_MU];
-  const double r0 = sqrt(c->sc_h[SC_RP2] + c->sc_h[SC_RD2]);
+  // N(gamma)'s references belong to the start point of the run, not to a resumed iterate
+  const double mu0 = resume ? resume->mu0 : c->sc_h[SC_MU];
+  const double r0 = resume ? resume->r0 : sqrt(c->sc_h[SC_RP2] + c->sc_h[SC_RD2]);
   lp_status result = LP_ERR_NOT_CONVERGED;
-  int k = 0;
+  int k = resume ? resume->k : 0;
   for (;;) {
     const double mu = c->sc_h[SC_MU];
     const double rpn = sqrt(c->sc_h[SC_RP2]), rdn = sqrt(c->sc_h[SC_RD2]);
@@ -1075,12 +1077,39 @@ extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, in
   inf.status = result;
   inf.stream_dtype = c->s_dtype;
   inf.stream_switch_iter = c->switch_iter;
+  c->ipm_state.k = k;
+  c->ipm_state.stream_switch_iter = c->switch_iter;
+  c->ipm_state.r0 = r0;
+  c->ipm_state.mu0 = mu0;
   LP_CU(cudaMemcpyAsync(x, c->x, n * sizeof(double), cudaMemcpyDefault, c->st));
   LP_CU(cudaMemcpyAsync(y, c->y, m * sizeof(double), cudaMemcpyDefault, c->st));
   LP_CU(cudaMemcpyAsync(s, c->s, n * sizeof(double), cudaMemcpyDefault, c->st));
   LP_CU(cudaStreamSynchronize(c->st));
   if (info) *info = inf;
   return result;
+}
+
+extern "C" lp_status lp_ipm_solve(lp_ctx* c, double* x, double* y, double* s, int32_t start_given,
+                                  lp_info* info) {
+  if (!c || !x || !y || !s) return fail(LP_ERR_ARG, "lp_ipm_solve: NULL argument");
+  return ipm_run(c, x, y, s, start_given != 0, nullptr, info);
+}
+
+extern "C" lp_status lp_ipm_get_state(lp_ctx* c, lp_ipm_state* state) {
+  if (!c || !state) return fail(LP_ERR_ARG, "lp_ipm_get_state: NULL argument");
+  *state = c->ipm_state;
+  return LP_OK;
+}
+
+extern "C" lp_status lp_ipm_resume(lp_ctx* c, double* x, double* y, double* s,
+                                   const lp_ipm_state* state, lp_info* info) {
+  if (!c || !x || !y || !s || !state) return fail(LP_ERR_ARG, "lp_ipm_resume: NULL argument");
+  if (state->k < 0 || !(state->r0 >= 0.0) || !isfinite(state->r0) || !(state->mu0 > 0.0) ||
+      !isfinite(state->mu0) || state->stream_switch_iter < -1 ||
+      state->stream_switch_iter > state->k)
+    return fail(LP_ERR_ARG, "lp_ipm_resume: state out of range");
+  const lp_ipm_state st = *state;   // the caller may pass the context's own state
+  return ipm_run(c, x, y, s, true, &st, info);
 }
 
 extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s, const double* p,

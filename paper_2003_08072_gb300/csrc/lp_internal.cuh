@@ -89,6 +89,7 @@ struct lp_ctx {
   int lda_s_req = 0;
   void* svals_req = nullptr;
   int switch_iter = -1;        // IPM iteration of the last switch (-1: none)
+  lp_ipm_state ipm_state{0, -1, 0.0, 0.0};  // Algorithm 2's state at the end of the last run
   bool use_staged = true;      // CG products through the shared-memory staged pass
   double mv_bytes_sum = 0.0;   // algorithmic bytes of the timed CG products
 

@@ -95,6 +95,17 @@ class LPSolver:
         """Algorithm 2 with host (numpy float64) iterate buffers, copied inside the call."""
         return B.lp_ipm_solve(self.ctx, x, y, s, start_given=start_given, check=check)
 
+    def state(self):
+        """Algorithm 2's state after the last solve or resume (a checkpoint with x, y, s)."""
+        return B.lp_ipm_get_state(self.ctx)
+
+    def resume(self, x, y, s, state, check: bool = True):
+        """Continues a solve from the iterate (x, y, s) (device) and its saved state; returns
+        (x, y, s, info) with info.ipm_iters the total iteration count."""
+        xv, yv, sv = x.clone(), y.clone(), s.clone()
+        info = B.lp_ipm_resume(self.ctx, xv, yv, sv, state, check=check)
+        return xv, yv, sv, info
+
     def residuals(self, x, y, s, sigma=None):
         sigma = self.params.sigma if sigma is None else sigma
         rp, rd, p = self._vec(self.m), self._vec(self.n), self._vec(self.m)

@@ -87,6 +87,15 @@ def test_argument_errors_need_no_device(lib):
         B.lp_create(4, 10, B.LP_CSR, B.LP_F64, 1, 1, 1, 4, 1, 1, params=bad)
     with pytest.raises(pkg.LPError):
         B.lp_sketch_indices(0, 0, 10, 3, 16, 1, 1)   # w % s != 0
+    # checkpoint / resume: plain-data state, NULL context rejected before any CUDA call
+    assert ctypes.sizeof(B.lp_ipm_state) == 24
+    with pytest.raises(pkg.LPError) as e:
+        B.lp_ipm_get_state(None)
+    assert e.value.status == B.LP_ERR_ARG
+    st = B.lp_ipm_state(k=3, stream_switch_iter=-1, r0=1.0, mu0=1.0)
+    with pytest.raises(pkg.LPError) as e:
+        B.lp_ipm_resume(None, 1, 1, 1, st)
+    assert e.value.status == B.LP_ERR_ARG
 
 
 def test_no_cpu_fallback_in_product_package():
