@@ -19,7 +19,7 @@
 // accumulator with an error-free TwoSum (the error term kept in a second accumulator), so a row
 // sum over the ~n/grid columns a CTA sees loses no more than a few FP32 units; the CTA sums go
 // to q with FP64 atomics.  Keeping the FP32-accumulated product near FP32 accuracy keeps CG's residual
-// recurrence close to the true residual, which spares most FP64 refinement passes.  The last
+// recurrence close to the true residual, which spares most FP64 refinement rounds.  The last
 // CTA forms d^T q and alpha; without a q buffer the sums go to per-CTA partials.
 //
 // Every wait on an mbarrier is bounded by the global timer; a wait that gives up sets
