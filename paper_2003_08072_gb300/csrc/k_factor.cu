@@ -117,14 +117,39 @@ __global__ void __launch_bounds__(256) k_gram_finish(const double* __restrict__ 
   }
 }
 
+// Largest split of the w columns gram_split may choose: >= 256 columns per split and at most
+// about 12 CTAs per SM in total (a host-only bound, also used to size the partial tiles).
+int gram_split_cap(int m, int w, int num_sms) {
+  const int nt = (m + kGT - 1) / kGT;
+  const int ntiles = nt * (nt + 1) / 2;
+  int cap = (12 * num_sms + ntiles - 1) / ntiles;
+  const int maxsplit = (w + 255) / 256;
+  if (cap > maxsplit) cap = maxsplit;
+  return cap < 1 ? 1 : cap;
+}
+
+// The split of the w columns.  At least enough splits for two CTAs per SM (while the cap
+// allows); beyond that, the split with the least estimated time: every CTA has the same work,
+// an SM works through its share of the CTAs at a steady rate, so the launch takes about
+// ceil(ctas / SMs) x (columns per split + one k-chunk of per-CTA overhead).  At m = 1000,
+// w = 4000 on 152 SMs: 10 splits (1360 CTAs, 9 per SM, 400 columns each) against 3 (408
+// CTAs, 3 per SM on 104 SMs but 2 on the other 48, 1344 columns each).
 int gram_split(int m, int w, int num_sms) {
   const int nt = (m + kGT - 1) / kGT;
   const int ntiles = nt * (nt + 1) / 2;
-  int split = (2 * num_sms + ntiles - 1) / ntiles;
-  const int maxsplit = (w + 255) / 256;   // keep >= 256 columns per split
-  if (split > maxsplit) split = maxsplit;
-  if (split < 1) split = 1;
-  return split;
+  const int cap = gram_split_cap(m, w, num_sms);
+  int base = (2 * num_sms + ntiles - 1) / ntiles;
+  if (base > cap) base = cap;
+  if (base < 1) base = 1;
+  auto cost = [&](int sp) {
+    const int64_t per_sm = ((int64_t)ntiles * sp + num_sms - 1) / num_sms;
+    const int64_t chunk = ((w + sp - 1) / sp + kGK - 1) / kGK * kGK;
+    return per_sm * (chunk + kGK);
+  };
+  int best = base;
+  for (int sp = base + 1; sp <= cap; ++sp)
+    if (cost(sp) < cost(best)) best = sp;
+  return best;
 }
 
 cudaError_t launch_gram(const double* G, float* Gdf, int ldg, int m, int w, int mp, double* Q,

@@ -1256,7 +1256,7 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   b += dn * s * (4 + 4 + 8) + 2.0 * kQCopies * dm * 8 + 3.0 * (w + 1) * 4; // sketch indices, q
   b += (double)round_up(m, 2) * w * 16 + (double)w * 8;                    // G, its split, u
   b += 3.0 * mp * mp * 8;                                                  // Q, M, X
-  b += (double)gram_split(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;
+  b += (double)gram_split_cap(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;
   b += (SC_COUNT + kMaxRedBlocks * 8) * 8.0 + FL_COUNT * 4 + 64;
   b += 8 * dm + 8 * dn;                                                    // b, c
   if (layout != LP_CSR) {

@@ -345,6 +345,7 @@ cudaError_t csr_to_csc(const int64_t* indptr, const int32_t* indices, const void
                        lp_dtype dt, int m, int64_t n, int64_t nnz, int64_t* colptr,
                        int64_t* cursor, int32_t* rowidx, void* cvals, cudaStream_t st);
 int gram_split(int m, int w, int num_sms);
+int gram_split_cap(int m, int w, int num_sms);
 
 // conversions
 cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, int m, int64_t n,
