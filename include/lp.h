@@ -40,7 +40,7 @@ typedef struct lp_ctx lp_ctx;
 typedef enum {
   LP_OK = 0,
   LP_ERR_ARG = 1,            /* bad argument: size, NULL, NaN/Inf input, unsupported combination */
-  LP_ERR_OOM = 2,            /* device allocation failed */
+  LP_ERR_OOM = 2,            /* device or host allocation failed (or over the serving budget) */
   LP_ERR_CUDA = 3,           /* a CUDA runtime call failed (message in lp_last_error) */
   LP_ERR_BREAKDOWN = 4,      /* factorization of the sketch met a non-positive pivot (rank(ADW) < m) */
   LP_ERR_NOT_CONVERGED = 5,  /* iteration cap reached; outputs hold the last iterate */
