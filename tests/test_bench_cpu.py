@@ -77,3 +77,17 @@ def test_preconditioned_kappa():
     lam, V = np.linalg.eigh(K)
     assert bench.preconditioned_kappa(K, V / np.sqrt(lam)) == pytest.approx(1.0, abs=1e-10)
     assert bench.preconditioned_kappa(-K, np.eye(30)) is None
+
+
+def test_traffic_figure_matches_its_profile_summary():
+    """The DRAM traffic bench.py reports comes from the committed ncu summary of the same
+    kernel source: the hash and the bytes per launch in bench.py and in the summary agree."""
+    import re
+
+    import bench
+
+    text = open(os.path.join(ROOT, "profiles",
+                             "k_cgprod_cg_product_dense_m1000_n200000_f32.md")).read()
+    assert bench.NCU_TRAFFIC["source_sha1"] in text
+    mb = float(re.search(r"traffic per launch \| \*\*([0-9.]+) MB\*\*", text).group(1))
+    assert abs(bench.NCU_TRAFFIC["bytes_per_launch"] - mb * 1e6) <= 0.01e6
