@@ -87,6 +87,11 @@ def test_argument_errors_need_no_device(lib):
         B.lp_create(4, 10, B.LP_CSR, B.LP_F64, 1, 1, 1, 4, 1, 1, params=bad)
     with pytest.raises(pkg.LPError):
         B.lp_sketch_indices(0, 0, 10, 3, 16, 1, 1)   # w % s != 0
+    # serving loop: bad sizes rejected before any CUDA call
+    for budget, live in ((0, 4), (1 << 30, 0), (1 << 30, 257)):
+        with pytest.raises(pkg.LPError) as e:
+            B.lp_server_create(budget, live)
+        assert e.value.status == B.LP_ERR_ARG
     # checkpoint / resume: plain-data state, NULL context rejected before any CUDA call
     assert ctypes.sizeof(B.lp_ipm_state) == 24
     with pytest.raises(pkg.LPError) as e:
