@@ -108,6 +108,11 @@ typedef struct {
   double f_target;         /* CG target of the last solve: min(cg_rel_tol ||f^(0)||, gamma sigma sqrt(mu)/(4 sqrt(n))) */
   int32_t stream_dtype;    /* lp_dtype the CG products streamed A in at exit (see lp_params.stream_dtype) */
   int32_t stream_switch_iter; /* IPM iteration at which the solve switched to the master copy; -1 if never */
+  int32_t factor_two_stage;   /* normal solves whose factor needed the second stage (Q numerically
+                                 singular for the one-stage inverse; see lp_factor) */
+  int32_t cg_precise_iter;    /* IPM iteration from which the CG products accumulated in FP64-class
+                                 arithmetic over the master copy, because FP64 refinement of FP32
+                                 products stopped contracting on the master copy itself; -1 if never */
 } lp_info;
 
 /* Fills *prm with the defaults listed above.  LP_ERR_ARG if prm is NULL. */
@@ -258,6 +263,12 @@ lp_status lp_sketch(lp_ctx* ctx, const double* d, int32_t k, double* G);
  *   Q    : device m*m float64 output or NULL (symmetric).
  *   Minv : device m*m float64 output or NULL (symmetric).
  * LP_ERR_BREAKDOWN if a pivot is not positive (rank(G) < m).  Synchronous.
+ * Inside lp_ipm_solve and lp_normal_solve, a Q that is numerically singular for this explicit
+ * inverse (a lost pivot, or ||Q Minv 1 - 1|| / sqrt(m) >= 1e-2; CountSketch reaches
+ * kappa(Q) ~ 1e17 late in the IPM) is factored in two stages instead: a shifted Cholesky
+ * factor L1 of Q whitens G into G1 = L1^{-1} G, a second Cholesky factor L2 of G1 G1^T
+ * follows, and the preconditioner is applied as X^T (X r) with X = L2^{-1} L1^{-1}, whose
+ * error grows with kappa(G) rather than kappa(Q) = kappa(G)^2 (lp_info.factor_two_stage).
  */
 lp_status lp_factor(lp_ctx* ctx, const double* G, double* Q, double* Minv);
 
@@ -299,15 +310,18 @@ lp_status lp_step(lp_ctx* ctx, double* x, double* y, double* s, const double* rd
  * outputs; the per-CTA partial sums live in one 4 MiB file-scope __device__ array of the
  * library, which every GPU that loads the library holds until the process exits.
  *   A      : device, column-major m x n with leading dimension lda (lda >= m), 16-byte aligned,
- *            lda * element size a multiple of 16 bytes.
+ *            lda * element size a multiple of 16 bytes.  The padding rows m..lda-1 are never
+ *            used (they may hold anything, NaN included).
  *   a_dtype: LP_F64 (FP64 accumulation) or LP_F32 / LP_BF16 / LP_F16 (FP32 accumulation).
  *   d2     : device n float64 (D^2).   v: device m float64.   y: device m float64 output.
  *   t      : device n float64 output or NULL.
  *   stream : cudaStream_t the two kernels are enqueued on.  Asynchronous.
  * Limit: m <= min(8192, 4 MiB / (accumulator bytes x SM count)), i.e. m <= 3449 for LP_F64 and
  * m <= 6898 otherwise on a 152-SM GB300; larger m returns LP_ERR_ARG with the limit in
- * lp_last_error().  The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.  All calls share the
+ * lp_last_error().  Each call made outside a stream capture looks up the array's device
+ * address (with the device current, so a device reset is harmless); a call during a capture
+ * reuses the address of the last call on that device, so make the first call on each device
+ * before any stream capture (else LP_ERR_ARG).  All calls share the
  * one array and each overwrites it completely, so calls whose kernels overlap on the GPU (two
  * streams, two threads) race and must be serialised by the caller.
  */
@@ -346,6 +360,21 @@ lp_status lp_profile_enable(lp_ctx* ctx, int32_t on);
 
 /* lp_profile_read -- copies the accumulated profile into *out (host); reset != 0 zeroes it. */
 lp_status lp_profile_read(lp_ctx* ctx, lp_profile* out, int32_t reset);
+
+/*
+ * lp_test_stall_copy -- failure-detection test hook (not part of the method).  The next CG
+ * product of this context that stages A through shared memory (a dense context streaming A
+ * below FP64) is launched with every bounded device-side wait limited to wait_ns nanoseconds
+ * (1 <= wait_ns <= 1e9; the normal limit is 1 s), and its first CTA never issues the bulk copy
+ * of its local column group `group` (0-based).  The wait for that copy then runs out, the
+ * kernel lets the copies it did issue land, returns without touching memory outside its
+ * buffers, and the call that ran the product (lp_normal_matvec, lp_normal_solve,
+ * lp_ipm_solve) returns LP_ERR_TIMEOUT with its outputs undefined; the context stays usable
+ * and later calls run normally.  No GPU fault is involved.  The hook is consumed by that one
+ * product; a group beyond the first CTA's share of columns injects nothing.
+ * LP_ERR_ARG for a NULL context, group < 0 or wait_ns outside the range.
+ */
+lp_status lp_test_stall_copy(lp_ctx* ctx, int32_t group, uint64_t wait_ns);
 
 /* ---------------- memory footprint and the serving loop ---------------- */
 

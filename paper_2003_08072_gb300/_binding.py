@@ -62,6 +62,8 @@ class lp_info(ctypes.Structure):
         ("f_target", ctypes.c_double),
         ("stream_dtype", ctypes.c_int32),
         ("stream_switch_iter", ctypes.c_int32),
+        ("factor_two_stage", ctypes.c_int32),
+        ("cg_precise_iter", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -160,6 +162,7 @@ _SIGNATURES = {
     "lp_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(lp_server_stats_t)]),
     "lp_server_destroy": (None, [_VP]),
     "lp_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(lp_profile), _I32]),
+    "lp_test_stall_copy": (ctypes.c_int, [_VP, _I32, ctypes.c_uint64]),
 }
 
 
@@ -303,6 +306,12 @@ def lp_profile_read(ctx, reset=False) -> lp_profile:
     p = lp_profile()
     _check(load().lp_profile_read(ctx, ctypes.byref(p), 1 if reset else 0))
     return p
+
+
+def lp_test_stall_copy(ctx, group, wait_ns):
+    """Failure-detection hook: the next staged CG product skips one bulk copy and its bounded
+    wait (wait_ns) runs out, so that call returns LP_ERR_TIMEOUT."""
+    _check(load().lp_test_stall_copy(ctx, int(group), int(wait_ns)))
 
 
 def lp_normal_matvec_noalloc(A, a_dtype, m, n, lda, d2, v, y, t=None, stream=None):

@@ -42,6 +42,22 @@ __device__ __forceinline__ void unpack(const uint4& r, ACC (&o)[VecN<TA>::N]) {
   }
 }
 
+// Zeroes the elements of a 16-byte vector from element `valid` on (1 <= valid): the rows at or
+// past m of a column whose leading dimension is padded, so that whatever the padding holds
+// (NaN or Inf included) cannot reach a sum.
+template <typename TA>
+__device__ __forceinline__ uint4 mask_tail(uint4 r, int valid) {
+  const int keep_bits = valid * (int)(sizeof(TA) * 8);
+  uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int lo = 32 * i;
+    if (keep_bits <= lo) w[i] = 0u;
+    else if (keep_bits < lo + 32) w[i] &= (1u << (keep_bits - lo)) - 1u;
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // Streaming 16-byte load (read once per pass: evict-first in L1 and L2).
 __device__ __forceinline__ uint4 ld_stream(const void* p) {
   return __ldcs(reinterpret_cast<const uint4*>(p));

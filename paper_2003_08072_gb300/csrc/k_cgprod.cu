@@ -86,15 +86,16 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s per wait
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s per wait unless ColArgs::wait_ns
 
-// Bounded wait for phase `parity` of bar.  Returns false (after the limit) if it never came.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// Bounded wait for phase `parity` of bar.  Returns false (after limit_ns) if it never came.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (unsigned spin = 1;; ++spin) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((spin & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    if ((spin & 255u) == 0 && global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -119,7 +120,11 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
   const int my_groups =
       blockIdx.x < ngroups ? (int)((ngroups - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
   const int64_t col_step = (int64_t)gridDim.x * TC;
+  const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
   auto issue = [&](int i, int stage) {   // thread 0: copy local group i into a stage
+    // fault-injection hook: CTA 0 never issues the copy of its group stall_group, so the
+    // wait for it runs out (its stage keeps stale data; nothing is written out of bounds)
+    if (blockIdx.x == 0 && (int64_t)i + 1 == a.stall_group_p1) return;
     const int64_t col0 = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * TC;
     const int ncols = (int)std::min<int64_t>(TC, a.n - col0);
     const unsigned bytes = (unsigned)((size_t)ncols * a.lda * sizeof(TA));
@@ -169,6 +174,7 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
 
   const int cl = lane % TC;
   bool timed_out = false;
+  int timeout_group = -1;   // the local group whose wait gave up (thread 0 issues the copies)
   // stage of group i is i % S and its phase parity (i / S) & 1, both kept as running counters
   int stage = 0, prev_stage = S - 1;
   unsigned parity = 0;
@@ -176,7 +182,10 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
   for (int i = 0; i < my_groups; ++i, col0 += col_step) {
     const TA* st = stages + (size_t)stage * stage_elems;
     // after one wait has given up, the rest are skipped (and no further copies issued)
-    if (!timed_out && !mbar_wait_bounded(&bars[stage], parity)) timed_out = true;
+    if (!timed_out && !mbar_wait_bounded(&bars[stage], parity, wait_ns)) {
+      timed_out = true;
+      timeout_group = i;
+    }
     const int ncols = (int)std::min<int64_t>(TC, a.n - col0);
     const int64_t mycol = col0 + cl;
     const bool cok = mycol < a.n;
@@ -264,9 +273,16 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
   if (s_timeout) {
     if (threadIdx.x == 0) {
       if (a.flw) a.flw[FL_TIMEOUT] = 1;
-      // let copies still in flight land before the CTA's shared memory goes away
-      for (int i = std::max(0, my_groups - S); i < my_groups; ++i)
-        mbar_wait_bounded(&bars[i % S], (unsigned)((i / S) & 1));
+      // let copies still in flight land before the CTA's shared memory goes away.  Thread 0
+      // issues every copy and waits for every group before it refills that group's stage, so
+      // if its own wait for group g gave up, groups g .. g + S - 2 were issued and not yet
+      // waited for, and nothing after them was issued; if thread 0 never gave up, it has
+      // already seen every copy land.
+      if (timeout_group >= 0) {
+        const int last = std::min(timeout_group + S - 2, my_groups - 1);
+        for (int i = timeout_group; i <= last; ++i)
+          mbar_wait_bounded(&bars[i % S], (unsigned)((i / S) & 1), wait_ns);
+      }
     }
     __syncthreads();
   }

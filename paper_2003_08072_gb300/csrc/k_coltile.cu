@@ -36,10 +36,12 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
   ACC yr[NOUT][SPW][VEC];
   int rowb[SPW];
   bool rok[SPW];
+  int tailv[SPW];   // rows of the slice's vector below m (VEC unless it straddles row m)
 #pragma unroll
   for (int sl = 0; sl < SPW; ++sl) {
     rowb[sl] = ((warp * SPW + sl) * 32 + lane) * VEC;
     rok[sl] = rowb[sl] < a.m;
+    tailv[sl] = min(VEC, a.m - rowb[sl]);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int row = rowb[sl] + e;
@@ -71,10 +73,13 @@ __global__ void __launch_bounds__(512) k_coltile(ColArgs a) {
       const int64_t col = col0 + c;
 #pragma unroll
       for (int sl = 0; sl < SPW; ++sl) {
-        if (col < a.n && rok[sl])
-          ar[c][sl] = ld_stream(A + col * a.lda + rowb[sl]);
-        else
+        if (col < a.n && rok[sl]) {
+          const uint4 r = ld_stream(A + col * a.lda + rowb[sl]);
+          // the padding rows m..lda-1 of a caller's matrix may hold anything
+          ar[c][sl] = tailv[sl] < VEC ? mask_tail<TA>(r, tailv[sl]) : r;
+        } else {
           ar[c][sl] = make_uint4(0u, 0u, 0u, 0u);
+        }
       }
     }
     // per-column operands for column col0 + (lane % TILE)

@@ -55,7 +55,16 @@ __global__ void __launch_bounds__(512) k_coltile_df(ColArgs a) {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int row = rowb[sl] + e;
-      split_double((rok[sl] && row < a.m) ? a.v[row] : 0.0, vh[sl][e], vl[sl][e]);
+      double x = 0.0;
+      if (rok[sl] && row < a.m) {
+        if (a.dz) {   // fused CG direction update d = z + beta d_old
+          x = fma(a.sc[SC_BETA], a.dold[row], a.dz[row]);
+          if (blockIdx.x == 0) a.dnew[row] = x;
+        } else {
+          x = a.v[row];
+        }
+      }
+      split_double(x, vh[sl][e], vl[sl][e]);
 #pragma unroll
       for (int o = 0; o < NOUT; ++o) ys[o][sl][e] = yc[o][sl][e] = 0.f;
     }

@@ -154,17 +154,117 @@ int gram_split(int m, int w, int num_sms) {
 
 cudaError_t launch_gram(const double* G, float* Gdf, int ldg, int m, int w, int mp, double* Q,
                         double* Qsplit, int split, cudaStream_t st) {
+  const size_t count = (size_t)ldg * w;
+  { note_launch(); k_split_df<<<2048, 256, 0, st>>>(G, count, Gdf, Gdf + count); }
+  return launch_gram_df(Gdf, ldg, m, w, mp, Q, Qsplit, split, st);
+}
+
+// Gram product of a sketch already held as hi / lo float planes (2 ldg w floats).
+cudaError_t launch_gram_df(const float* Gdf, int ldg, int m, int w, int mp, double* Q,
+                           double* Qsplit, int split, cudaStream_t st) {
   const int nt = mp / kGT;
   const int ntiles = nt * (nt + 1) / 2;
   int chunk = (w + split - 1) / split;
   chunk = (chunk + kGK - 1) / kGK * kGK;
   const size_t count = (size_t)ldg * w;
-  float* Gh = Gdf;
-  float* Gl = Gdf + count;
-  { note_launch(); k_split_df<<<2048, 256, 0, st>>>(G, count, Gh, Gl); }
+  const float* Gh = Gdf;
+  const float* Gl = Gdf + count;
   dim3 grid(ntiles, split);
   { note_launch(); k_gram_tile<<<grid, 256, 0, st>>>(Gh, Gl, ldg, m, w, chunk, Qsplit, ntiles); }
   { note_launch(); k_gram_finish<<<ntiles, 256, 0, st>>>(Qsplit, split, ntiles, m, mp, Q); }
+  return cudaGetLastError();
+}
+
+// ---- products with a triangular double-float factor ---------------------------------------
+//
+// C = A B with A lower triangular (double-float planes, row-major) and B given by strides,
+// in double-float arithmetic on the FP32 pipes: 64 x 64 tiles of C, 16-deep chunks of the
+// inner index, the k range cut to where neither factor is structurally zero.  Used by the
+// second factor stage below: G1 = X1 G (the sketch whitened by the first stage's inverse
+// factor) and X = X2 X1 (the inverse factor of both stages together).
+__global__ void __launch_bounds__(256) k_df_trmm(TrmmArgs a) {
+  __shared__ __align__(16) float sAh[kGK][kGT + 4];
+  __shared__ __align__(16) float sAl[kGK][kGT + 4];
+  __shared__ __align__(16) float sBh[kGK][kGT + 4];
+  __shared__ __align__(16) float sBl[kGK][kGT + 4];
+  const int jb = blockIdx.x, ib = blockIdx.y;
+  const int row0 = ib * kGT, col0 = jb * kGT;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // A[i][k] = 0 for k > i; with b_lower, B[k][j] = 0 for k < j
+  const int kend = min(a.K, row0 + kGT);
+  const int kbeg = a.b_lower ? col0 : 0;
+  const bool b_rowmajor = (a.sbj == 1);
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[i][j] = c[i][j] = 0.f;
+  for (int k = kbeg; k < kend; k += kGK) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int idx = tid + l * 256;
+      {
+        const int r = idx >> 4, kk = idx & 15;
+        const int row = row0 + r, kx = k + kk;
+        const bool v = row < a.M && kx < kend;
+        const size_t ia = (size_t)row * a.lda + kx;
+        sAh[kk][r] = v ? a.Ah[ia] : 0.f;
+        sAl[kk][r] = v ? a.Al[ia] : 0.f;
+      }
+      {
+        const int kk = b_rowmajor ? (idx >> 6) : (idx & 15);
+        const int cc = b_rowmajor ? (idx & 63) : (idx >> 4);
+        const int kx = k + kk, col = col0 + cc;
+        const bool v = kx < kend && col < a.N;
+        const size_t ibb = (size_t)kx * a.sbk + (size_t)col * a.sbj;
+        sBh[kk][cc] = v ? a.Bh[ibb] : 0.f;
+        sBl[kk][cc] = v ? a.Bl[ibb] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kGK; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = sAh[kk][ty * 4 + i];
+        al[i] = sAl[kk][ty * 4 + i];
+        bh[i] = sBh[kk][tx * 4 + i];
+        bl[i] = sBl[kk][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_mac(ah[i], al[i], bh[j], bl[j], s[i][j], c[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) df_renorm(s[i][j], c[i][j]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = row0 + ty * 4 + i, col = col0 + tx * 4 + j;
+      if (row >= a.M || col >= a.N) continue;
+      const size_t o = (size_t)row * a.sci + (size_t)col * a.scj;
+      a.Ch[o] = s[i][j];
+      a.Cl[o] = c[i][j];
+      if (a.Th) {
+        const size_t o2 = (size_t)row * a.sti + (size_t)col * a.stj;
+        a.Th[o2] = s[i][j];
+        a.Tl[o2] = c[i][j];
+      }
+    }
+}
+
+cudaError_t launch_df_trmm(const TrmmArgs& a, cudaStream_t st) {
+  if (a.M < 1 || a.N < 1) return cudaSuccess;
+  dim3 grid((a.N + kGT - 1) / kGT, (a.M + kGT - 1) / kGT);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  { note_launch(); k_df_trmm<<<grid, 256, 0, st>>>(a); }
   return cudaGetLastError();
 }
 

@@ -19,22 +19,36 @@ constexpr size_t kScratchBytes = size_t(4) << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // In host code g_scratch is only a host-side stand-in for the device symbol; its device
-// address is looked up once per device (with that device current) and cached here.
+// address is looked up with the device current.  The lookup is repeated on every call made
+// outside a stream capture (the address changes if the context is torn down and re-created,
+// e.g. after cudaDeviceReset); during a capture the address cached by the last such call is
+// used, so the first call on a device must come before any capture.
 constexpr int kMaxDevices = 64;
 void* g_scratch_dev[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
 std::mutex g_setup_mu;
 
-lp_status setup_device(int dev) {
+lp_status setup_device(int dev, cudaStream_t stream) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (g_scratch_dev[dev]) return LP_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;   // unknown: do not touch the cache
+  }
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (g_scratch_dev[dev]) return LP_OK;
+    lp_set_error("lp_normal_matvec_noalloc: the first call on a device must precede stream capture");
+    return LP_ERR_ARG;
+  }
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess || !p) return lp_cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-  int sms = 0;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return lp_cuda_fail(e, "cudaDeviceGetAttribute");
-  g_num_sms[dev] = sms;
+  if (!g_num_sms[dev]) {
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return lp_cuda_fail(e, "cudaDeviceGetAttribute");
+    g_num_sms[dev] = sms;
+  }
   g_scratch_dev[dev] = p;
   return LP_OK;
 }
@@ -68,7 +82,7 @@ extern "C" lp_status lp_normal_matvec_noalloc(const void* A, lp_dtype a_dtype, i
     lp_set_error("lp_normal_matvec_noalloc: device ordinal beyond 63");
     return LP_ERR_ARG;
   }
-  lp_status st = setup_device(dev);
+  lp_status st = setup_device(dev, (cudaStream_t)stream);
   if (st != LP_OK) return st;
   // Each CTA writes m partial sums of the accumulator type; the grid must fit the scratch.
   const size_t acc = (a_dtype == LP_F64) ? 8 : 4;

@@ -165,13 +165,18 @@ struct SymvArgs {
   double* dy;
   const double* qf;    // the product's atomic q copies (q itself holds their sum)
   double* qzero;       // zeroed by CTA 0 for the next CG product
+  // factored preconditioner M = X^T X (X = L^{-1}, lower triangular): the first of its two
+  // products, t = X r, forms rho = r^T M r as ||t||^2 (sq); the second, z = X^T t, does no
+  // bookkeeping and is skipped once the solve has finished (skip_done)
+  int sq;
+  int skip_done;
 };
 
 // DF: M holds double-float pairs (Mh = (float*)M, Ml = Mh + mp^2) and the row sums run on the
 // FP32 pipes; otherwise M is FP64.
 template <bool DF>
 __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
-  if (a.mode == SYMV_CG_STEP && a.fl[FL_DONE]) return;
+  if ((a.mode == SYMV_CG_STEP || a.skip_done) && a.fl[FL_DONE]) return;
   extern __shared__ double rs[];
   const int m4 = (a.m + 3) & ~3;                      // rows of M are padded (mp >= m4)
   float* rh = reinterpret_cast<float*>(rs + m4);      // DF: r split into hi / lo floats
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
     }
     if (lane == 0) {
       a.z[row] = acc;
-      dotc = acc * rs[row];
+      dotc = a.sq ? acc * acc : acc * rs[row];
     }
   }
   if (a.mode == SYMV_PLAIN) return;
@@ -312,6 +317,28 @@ cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, do
              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const size_t smem = (size_t)((m + 3) & ~3) * 2 * sizeof(double);
   { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a); }
+  return cudaGetLastError();
+}
+
+// Factored preconditioner M = X^T X with X = L^{-1} of both factor stages (double-float,
+// row-major X and its transpose XT): t = X r carries the CG bookkeeping of `mode` with
+// rho = ||t||^2 = r^T M r, then z = X^T t.  For SYMV_CG_STEP the residual update is fused
+// into the first product exactly as in launch_symv_cg_step.
+cudaError_t launch_precond_factored(const double* X, const double* XT, int mp, int m, int mode,
+                                    const double* r, double* t, double* z, double* sc, int* fl,
+                                    double* bpart, unsigned* bcnt, double rel_tol,
+                                    cudaStream_t st, const double* rold, const double* q,
+                                    const double* d, double* dy, const double* qf,
+                                    double* qzero) {
+  SymvArgs a1{X, mp, m, r, t, sc, fl, bpart, bcnt, mode, rel_tol * rel_tol, rold, q, d, dy, qf,
+              qzero, 1, 0};
+  const size_t smem = (size_t)((m + 3) & ~3) * 2 * sizeof(double);
+  { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a1); }
+  // the second product finishes an unfinished CG step; for SYMV_F2 / SYMV_PLAIN z is wanted
+  const int skip = (mode == SYMV_CG_STEP || mode == SYMV_CG_INIT) ? 1 : 0;
+  SymvArgs a2{XT, mp, m, t, z, sc, fl, bpart, bcnt, SYMV_PLAIN, 0.0, nullptr, nullptr, nullptr,
+              nullptr, nullptr, nullptr, 0, skip};
+  { note_launch(); k_symv<true><<<(m + 7) / 8, 256, smem, st>>>(a2); }
   return cudaGetLastError();
 }
 

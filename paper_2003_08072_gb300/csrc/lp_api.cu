@@ -193,7 +193,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
-                  c->bcnt};
+                  c->bcnt, c->X1, c->XF, c->XFT, c->G1df, c->ptmp};
   for (void* p : bufs) dfree(p);
   pinned_release(c->pin_blk);
   for (auto& pr : c->ev_pending) {
@@ -215,7 +215,8 @@ static lp_status alloc_workspace(lp_ctx* c) {
   for (double** p : nvec) LP_TRY(dalloc(p, (size_t)n));
   LP_TRY(dalloc(&c->d2f, (size_t)n));
   double** mvec[] = {&c->y, &c->rp, &c->p, &c->dy, &c->r, &c->z, &c->dd, &c->q, &c->rtil,
-                     &c->qhat, &c->res, &c->tm, &c->dyacc, &c->rhs, &c->r_alt, &c->d_alt};
+                     &c->qhat, &c->res, &c->tm, &c->dyacc, &c->rhs, &c->r_alt, &c->d_alt,
+                     &c->ptmp};
   for (double** p : mvec) LP_TRY(dalloc(p, (size_t)m));
   const int maxgrid = std::max(coltile_max_grid(c->num_sms), csc_max_grid(c->num_sms));
   c->part_bytes = (size_t)maxgrid * 2 * m * sizeof(double);
@@ -584,8 +585,15 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
       qacc = nullptr;
     }
     nblk = -1;
-    if (!acc64 && a.d2f && c->use_staged)
+    if (!acc64 && a.d2f && c->use_staged) {
+      a.stall_group_p1 = c->stall_group_p1;   // fault injection: next staged product only
+      a.wait_ns = c->stall_wait_ns;
       nblk = launch_cgprod(ta, a, c->num_sms, coltile_max_grid(c->num_sms), c->st);
+      if (nblk >= 0) {
+        c->stall_group_p1 = 0;
+        c->stall_wait_ns = 0;
+      }
+    }
     if (nblk < 0) nblk = launch_coltile(ta, acc64, MODE_NORMAL, a, c->num_sms, c->st);
   } else {
     CscArgs a{};
@@ -688,6 +696,8 @@ static void stream_reset(lp_ctx* c) {
   c->svals = c->svals_req;
   c->cs2_on = c->cs2 != nullptr;
   c->switch_iter = -1;
+  c->cg_precise = false;
+  c->precise_iter = -1;
 }
 
 // Stream the master copy instead (FP32 for an FP32 input, FP64 for an FP64 one) for the rest
@@ -787,33 +797,172 @@ static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
   return LP_OK;
 }
 
-// Alg. 1 step 2: Q = G G^T, M = Q^{-1}.  With allow_shift, a lost pivot (Q numerically
-// singular) is retried with M = (Q + eps diag(Q))^{-1}, eps = 1e-10, 1e-8, ..., 1e-4: M is
-// then only a preconditioner, and (A D W)^dagger is applied by PCG on Q itself.
+// Probe check of a factor stage: ||(Q + eps diag Q)(M 1) - 1|| / sqrt(m) and the pivot flag.
+static lp_status factor_check(lp_ctx* c, double eps, double* qerr, bool* brk) {
+  LP_CU(launch_vec_ops(VOP_ONES, c->res, nullptr, nullptr, c->m, nullptr, c->st));
+  LP_CU(launch_symv_dot(c->M, c->mp, c->m, c->res, c->tm, c->sc, c->fl, c->bpart, c->bcnt,
+                        SYMV_PLAIN, c->st));
+  LP_CU(launch_symv_f64(c->Q, c->mp, c->m, c->tm, c->rhs, c->st));
+  if (eps > 0.0) LP_CU(launch_add_shift(c->rhs, c->Q, c->mp, c->m, eps, c->tm, c->st));
+  LP_CU(launch_vec_ops(VOP_SUB, c->rhs, c->rhs, c->res, c->m, nullptr, c->st));
+  LP_CU(launch_norm2(c->rhs, c->m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
+  LP_TRY(sync_scalars(c));
+  *qerr = sqrt(c->sc_h[SC_RES2] / (double)c->m);
+  *brk = c->fl_h[FL_BREAK] != 0;
+  return LP_OK;
+}
+
+// Buffers of the second factor stage, allocated on first use.
+static lp_status ensure_stage2(lp_ctx* c) {
+  if (c->X1 && c->XF && c->XFT && c->G1df) return LP_OK;
+  AllocStream as(c->st);
+  const size_t mm = (size_t)c->mp * c->mp;
+  if (!c->X1) LP_TRY(dalloc(&c->X1, mm));
+  if (!c->XF) LP_TRY(dalloc(&c->XF, mm));
+  if (!c->XFT) LP_TRY(dalloc(&c->XFT, mm));
+  if (!c->G1df) {
+    LP_TRY(dalloc(&c->G1df, (size_t)2 * c->ldg * c->w));
+    // rows m..ldg-1 of G1 are never written and must read as zero
+    LP_CU(cudaMemsetAsync(c->G1df, 0, (size_t)2 * c->ldg * c->w * sizeof(float), c->st));
+  }
+  return LP_OK;
+}
+
+// Probe error below which a one-stage factor M = Q^{-1} serves as the preconditioner.
+constexpr double kDirectQerr = 1e-2;
+
+// Alg. 1 step 2: Q = G G^T, M = Q^{-1} (Eq. pdprecond).  The Gram route squares kappa(G), so
+// once Q is numerically singular in double-float (a lost pivot, or a probe error above
+// kDirectQerr; CountSketch reaches kappa(Q) ~ 1e17 late in the IPM) the factor takes a second
+// stage, in the manner of CholeskyQR2 with a shifted first step:
+//   stage 1: (Q + eps1 diag Q) = L1 L1^T, X1 = L1^{-1} (eps1 = 1e-10, raised until no pivot is
+//            lost);
+//   stage 2: G1 = X1 G, Q2 = G1 G1^T (kappa(Q2) ~ eps1 kappa(Q) instead of kappa(Q)),
+//            Q2 = L2 L2^T, X2 = L2^{-1};
+// then X = X2 X1 satisfies X G G^T X^T = I up to ~u kappa(G) (u the double-float unit), and
+// the preconditioner is applied as X^T (X r): two triangular products whose error grows with
+// kappa(G) = kappa(Q)^{1/2}, where the explicit inverse of the one-stage route grows with
+// kappa(Q).  Without allow_shift (lp_factor) only the one-stage inverse is formed and a lost
+// pivot is an error.  If stage 2 itself loses a pivot, it falls back to a shifted M2 =
+// (Q2 + eps diag Q2)^{-1}, eps = 1e-10 ... 1e-4: M is then only a preconditioner, and
+// (A D W)^dagger is still applied exactly, by PCG on Q through G.
 static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
   PhaseScope ps(c, LP_PH_FACTOR);
+  c->factored = false;
+  c->factor_stages = 1;
   LP_CU(launch_gram(G, c->Gdf, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
+  double qerr = 0.0;
+  bool brk = false;
+  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
+  LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, 0.0, c->fl, c->st));
+  LP_TRY(factor_check(c, 0.0, &qerr, &brk));
+  c->qerr = qerr;
+  c->shift = 0.0;
+  if (!brk && qerr < (allow_shift ? kDirectQerr : 0.5)) return LP_OK;
+  if (!allow_shift)
+    return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (pivot lost in the inverse)");
+  LP_TRY(ensure_stage2(c));
+  const size_t mm = (size_t)c->mp * c->mp;
+  // stage 1: the shifted factor
+  double eps1 = 1e-10;
+  for (;;) {
+    LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
+    LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps1, c->fl, c->st));
+    LP_TRY(sync_scalars(c));
+    if (!c->fl_h[FL_BREAK]) break;
+    eps1 *= 100.0;
+    if (eps1 > 1e-4)
+      return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (shifted first stage lost a pivot)");
+  }
+  LP_CU(cudaMemcpyAsync(c->X1, c->X, mm * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  // G1 = X1 G from the hi / lo planes of G that the Gram product left in Gdf
+  {
+    TrmmArgs t{};
+    t.Ah = reinterpret_cast<const float*>(c->X1);
+    t.Al = t.Ah + mm;
+    t.lda = c->mp;
+    t.Bh = c->Gdf;
+    t.Bl = c->Gdf + (size_t)c->ldg * c->w;
+    t.sbk = 1;
+    t.sbj = c->ldg;
+    t.M = c->m;
+    t.N = c->w;
+    t.K = c->m;
+    t.b_lower = 0;
+    t.Ch = c->G1df;
+    t.Cl = c->G1df + (size_t)c->ldg * c->w;
+    t.sci = 1;
+    t.scj = c->ldg;
+    LP_CU(launch_df_trmm(t, c->st));
+  }
+  LP_CU(launch_gram_df(c->G1df, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
+  // stage 2
   double eps = 0.0;
   for (;;) {
     LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
     LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps, c->fl, c->st));
-    // a-posteriori check on a fixed probe v = 1: ||(Q + eps diag Q)(M v) - v|| / ||v|| must be
-    // small, i.e. M must be an accurate inverse of the (shifted) matrix it was computed from
-    LP_CU(launch_vec_ops(VOP_ONES, c->res, nullptr, nullptr, c->m, nullptr, c->st));
-    LP_CU(launch_symv_dot(c->M, c->mp, c->m, c->res, c->tm, c->sc, c->fl, c->bpart, c->bcnt,
-                          SYMV_PLAIN, c->st));
-    LP_CU(launch_symv_f64(c->Q, c->mp, c->m, c->tm, c->rhs, c->st));
-    if (eps > 0.0) LP_CU(launch_add_shift(c->rhs, c->Q, c->mp, c->m, eps, c->tm, c->st));
-    LP_CU(launch_vec_ops(VOP_SUB, c->rhs, c->rhs, c->res, c->m, nullptr, c->st));
-    LP_CU(launch_norm2(c->rhs, c->m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
-    LP_TRY(sync_scalars(c));
-    const double qerr = sqrt(c->sc_h[SC_RES2] / (double)c->m);
-    if (!c->fl_h[FL_BREAK] && qerr < 0.5) break;
+    LP_TRY(factor_check(c, eps, &qerr, &brk));
+    if (!brk && qerr < 0.5) break;
     eps = eps > 0.0 ? eps * 100.0 : 1e-10;
-    if (!allow_shift || eps > 1e-4)
-      return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (pivot lost in the inverse)");
+    if (eps > 1e-4)
+      return fail(LP_ERR_BREAKDOWN, "sketch A D W is rank deficient (pivot lost in the second stage)");
   }
+  // X = X2 X1 (lower triangular) and its transpose, for z = X^T (X r)
+  {
+    TrmmArgs t{};
+    t.Ah = reinterpret_cast<const float*>(c->X);
+    t.Al = t.Ah + mm;
+    t.lda = c->mp;
+    t.Bh = reinterpret_cast<const float*>(c->X1);
+    t.Bl = t.Bh + mm;
+    t.sbk = c->mp;
+    t.sbj = 1;
+    t.M = c->mp;
+    t.N = c->mp;
+    t.K = c->mp;
+    t.b_lower = 1;
+    t.Ch = reinterpret_cast<float*>(c->XF);
+    t.Cl = t.Ch + mm;
+    t.sci = c->mp;
+    t.scj = 1;
+    t.Th = reinterpret_cast<float*>(c->XFT);
+    t.Tl = t.Th + mm;
+    t.sti = 1;
+    t.stj = c->mp;
+    LP_CU(launch_df_trmm(t, c->st));
+  }
+  c->factored = true;
+  c->factor_stages = 2;
   c->shift = eps;
+  c->qerr = qerr;
+  return LP_OK;
+}
+
+// Preconditioner apply z = M r with the bookkeeping of `mode` (SYMV_CG_INIT, SYMV_F2,
+// SYMV_PLAIN), through the explicit inverse or the two-stage factor.
+static lp_status precond_apply(lp_ctx* c, int mode, const double* r, double* z, double rel_tol) {
+  if (c->factored)
+    LP_CU(launch_precond_factored(c->XF, c->XFT, c->mp, c->m, mode, r, c->ptmp, z, c->sc, c->fl,
+                                  c->bpart, c->bcnt, rel_tol, c->st));
+  else if (mode == SYMV_CG_INIT)
+    LP_CU(launch_symv_init(c->M, c->mp, c->m, r, z, c->sc, c->fl, c->bpart, c->bcnt, rel_tol,
+                           c->st));
+  else
+    LP_CU(launch_symv_dot(c->M, c->mp, c->m, r, z, c->sc, c->fl, c->bpart, c->bcnt, mode, c->st));
+  return LP_OK;
+}
+
+// CG step r_new = r_old - alpha q, dy += alpha d, z = M r_new, rho and beta.
+static lp_status precond_cg_step(lp_ctx* c, const double* rold, const double* q, const double* d,
+                                 double* dy, double* rnew, double* z, const double* qf,
+                                 double* qzero) {
+  if (c->factored)
+    LP_CU(launch_precond_factored(c->XF, c->XFT, c->mp, c->m, SYMV_CG_STEP, rnew, c->ptmp, z,
+                                  c->sc, c->fl, c->bpart, c->bcnt, 0.0, c->st, rold, q, d, dy,
+                                  qf, qzero));
+  else
+    LP_CU(launch_symv_cg_step(c->M, c->mp, c->m, rold, q, d, dy, rnew, z, c->sc, c->fl, c->bpart,
+                              c->bcnt, c->st, qf, qzero));
   return LP_OK;
 }
 
@@ -836,15 +985,14 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
   const bool rich = op == 0 && c->prm.inner_solver == LP_INNER_RICHARDSON;
   LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_RICH, rich ? 1 : 0, c->st));
   LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_DIVERGED, 0, c->st));
-  LP_CU(launch_symv_init(c->M, c->mp, m, c->r, c->z, c->sc, c->fl, c->bpart, c->bcnt, rel_tol,
-                         c->st));
+  LP_TRY(precond_apply(c, SYMV_CG_INIT, c->r, c->z, rel_tol));
   // d starts at 0 so that the first fused direction update (beta = 0) gives d = z
   LP_CU(launch_vec_ops(VOP_ZERO, c->d_alt, nullptr, nullptr, m, nullptr, c->st));
   // iteration j: d_j = z + beta d_{j-1} into dbuf[j & 1]; r_{j+1} into rbuf[(j + 1) & 1]
   double* rbuf[2] = {c->r, c->r_alt};
   double* dbuf[2] = {c->dd, c->d_alt};
   // FP32-accumulated dense products reduce themselves into qbuf with atomics
-  const bool atomic_q = (op == 0) && !c->sparse && c->s_dtype != LP_F64;
+  const bool atomic_q = (op == 0) && !c->sparse && c->s_dtype != LP_F64 && !c->cg_precise;
   double* qbuf[2] = {c->qf, c->qf + (size_t)kQCopies * m};
   if (atomic_q) LP_CU(cudaMemsetAsync(c->qf, 0, (size_t)kQCopies * m * sizeof(double), c->st));
   int done_before = 0;
@@ -854,15 +1002,14 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
       double* dnew = dbuf[j & 1];
       const double* dold = dbuf[(j + 1) & 1];
       if (op == 0)
-        LP_TRY(pass_normal(c, false, nullptr, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1, true,
-                           c->z, dold, dnew, atomic_q ? qbuf[j & 1] : nullptr));
+        LP_TRY(pass_normal(c, c->cg_precise, nullptr, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1,
+                           true, c->z, dold, dnew, atomic_q ? qbuf[j & 1] : nullptr));
       else
         LP_TRY(pass_gram(c, c->G, nullptr, nullptr, c->q, nullptr, RED_CG_Q, 1, c->z, dold,
                          dnew));
-      LP_CU(launch_symv_cg_step(c->M, c->mp, m, rbuf[j & 1], c->q, dnew, delta,
-                                rbuf[(j + 1) & 1], c->z, c->sc, c->fl, c->bpart, c->bcnt, c->st,
-                                atomic_q ? qbuf[j & 1] : nullptr,
-                                atomic_q ? qbuf[(j + 1) & 1] : nullptr));
+      LP_TRY(precond_cg_step(c, rbuf[j & 1], c->q, dnew, delta, rbuf[(j + 1) & 1], c->z,
+                             atomic_q ? qbuf[j & 1] : nullptr,
+                             atomic_q ? qbuf[(j + 1) & 1] : nullptr));
     }
     LP_TRY(sync_scalars(c));
     if (!c->mv_pending.empty()) prof_harvest_mv(c, c->fl_h[FL_ITERS] - done_before);
@@ -896,7 +1043,7 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
   double abs_thr = INFINITY;
   if (c->prm.cg_theory_rule)
     abs_thr = c->prm.gamma * c->prm.sigma * sqrt(mu) / (4.0 * sqrt((double)c->n));
-  bool lowprec = c->s_dtype != LP_F64;   // CG products accumulate in FP32
+  bool lowprec = c->s_dtype != LP_F64 && !c->cg_precise;   // CG products accumulate in FP32
   double rho0 = 0.0, target2 = 0.0, f2_prev = INFINITY, contraction = 0.0;
   int total_it = 0, outer = 0, passes = 0;
   for (;;) {
@@ -926,8 +1073,7 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
       LP_TRY(pass_normal(c, true, c->dyacc, c->d2, c->t, RED_MINUS_P, c->rtil, p, 0));
     }
     // ||f||^2 = r~^T Q^{-1} r~; qhat = Q^{-1} r~ starts the correction
-    LP_CU(launch_symv_dot(c->M, c->mp, m, c->rtil, c->qhat, c->sc, c->fl, c->bpart, c->bcnt,
-                          SYMV_F2, c->st));
+    LP_TRY(precond_apply(c, SYMV_F2, c->rtil, c->qhat, 0.0));
     LP_TRY(sync_scalars(c));
     const double f2 = c->sc_h[SC_F2];
     if (!isfinite(f2)) return fail(LP_ERR_NUMERIC, "non-finite residual in the normal solve");
@@ -944,13 +1090,18 @@ static lp_status run_normal_solve(lp_ctx* c, const double* p, int k, double mu, 
     contraction = sqrt(f2 / (passes == 0 ? std::max(rho0, 1e-300) : f2_prev));
     const bool stalled = (passes == 0 && contraction > 0.125) || (passes >= 1 && f2 > 0.25 * f2_prev);
     if (stalled || passes >= c->prm.refine_max) {
-      if (!stream_switch(c, k)) {
-        if (passes >= c->prm.refine_max) break;
-      } else {
+      if (stream_switch(c, k)) {
         lowprec = c->s_dtype != LP_F64;
-        passes = 0;
-        contraction = 0.0;   // the master copy's passes solve to the target
+      } else {
+        // refinement stalls on the master copy itself (FP32 A): the CG products accumulate in
+        // FP64-class arithmetic from here on, for the rest of the IPM, and the next pass
+        // solves the correction to the target
+        c->cg_precise = true;
+        c->precise_iter = k;
+        lowprec = false;
       }
+      passes = 0;
+      contraction = 0.0;   // the master copy's passes solve to the target
     }
     f2_prev = f2;
     ++outer;
@@ -1048,6 +1199,8 @@ static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_
     }
     inf.cg_iters_total += so.cg_iters;
     inf.cg_iters_last = so.cg_iters;
+    if (c->factor_stages == 2) inf.factor_two_stage += 1;
+    inf.cg_precise_iter = c->precise_iter;
     inf.refine_steps = so.refine;
     inf.f_norm = so.f_norm;
     inf.f_target = so.f_target;
@@ -1077,6 +1230,7 @@ static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_
   inf.status = result;
   inf.stream_dtype = c->s_dtype;
   inf.stream_switch_iter = c->switch_iter;
+  inf.cg_precise_iter = c->precise_iter;
   c->ipm_state.k = k;
   c->ipm_state.stream_switch_iter = c->switch_iter;
   c->ipm_state.r0 = r0;
@@ -1147,6 +1301,8 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
     inf.mu = mu;
     inf.stream_dtype = c->s_dtype;
     inf.stream_switch_iter = c->switch_iter;
+    inf.factor_two_stage = c->factor_stages == 2 ? 1 : 0;
+    inf.cg_precise_iter = c->precise_iter;
     *info = inf;
   }
   return LP_OK;
@@ -1215,7 +1371,14 @@ extern "C" lp_status lp_normal_matvec(lp_ctx* c, const double* d2, const double*
   }
   LP_TRY(pass_normal(c, precise, v, d2, t, RED_PLAIN, y, nullptr, 0, false, nullptr, nullptr,
                      nullptr, nullptr, !precise && c->s_dtype != LP_F64));
-  LP_CU(cudaStreamSynchronize(c->st));
+  return sync_scalars(c);   // LP_ERR_TIMEOUT if a bounded wait of the product gave up
+}
+
+extern "C" lp_status lp_test_stall_copy(lp_ctx* c, int32_t group, uint64_t wait_ns) {
+  if (!c || group < 0 || wait_ns == 0 || wait_ns > 1000000000ull)
+    return fail(LP_ERR_ARG, "lp_test_stall_copy: need a context, group >= 0, 0 < wait_ns <= 1e9");
+  c->stall_group_p1 = (int64_t)group + 1;
+  c->stall_wait_ns = wait_ns;
   return LP_OK;
 }
 

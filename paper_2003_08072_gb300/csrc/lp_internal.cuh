@@ -89,8 +89,15 @@ struct lp_ctx {
   int lda_s_req = 0;
   void* svals_req = nullptr;
   int switch_iter = -1;        // IPM iteration of the last switch (-1: none)
+  // last resort of the refinement: CG products with FP64-class accumulation over the master
+  // copy (double-float for FP32 A) once refinement stalls on the master copy itself
+  bool cg_precise = false;
+  int precise_iter = -1;       // IPM iteration of that escalation (-1: none)
   lp_ipm_state ipm_state{0, -1, 0.0, 0.0};  // Algorithm 2's state at the end of the last run
   bool use_staged = true;      // CG products through the shared-memory staged pass
+  // fault injection for the next staged CG product only (lp_test_stall_copy)
+  int64_t stall_group_p1 = 0;
+  uint64_t stall_wait_ns = 0;
   double mv_bytes_sum = 0.0;   // algorithmic bytes of the timed CG products
 
   // CSC (sparse) copy: column pointers, row ids, values
@@ -141,6 +148,17 @@ struct lp_ctx {
   double* Qsplit = nullptr;    // split-k partials of the Gram product
   int qsplit = 1;
   double shift = 0.0;          // relative diagonal shift used by the last factorization
+  // second factor stage (Q numerically singular for the Gram route, e.g. CountSketch late in
+  // the IPM): X1 = inverse factor of the shifted first stage, G1 = X1 G as hi / lo planes,
+  // XF = X2 X1 and its transpose XFT (double-float planes, mp x mp); allocated on first use
+  bool factored = false;       // the preconditioner is applied as XF^T (XF r)
+  int factor_stages = 1;       // stages of the last factorization (1 or 2)
+  double qerr = 0.0;           // probe error ||Q M 1 - 1|| / sqrt(m) of the last factor stage
+  double* X1 = nullptr;
+  double* XF = nullptr;
+  double* XFT = nullptr;
+  float* G1df = nullptr;
+  double* ptmp = nullptr;      // m-vector: X r of the factored apply
 
   // scalars
   double* sc = nullptr;        // device SC_COUNT
@@ -210,6 +228,11 @@ struct ColArgs {
   unsigned* cnt;
   double* scw;
   int* flw;
+  // staged CG product only: limit of each bounded wait (0: 1 s), and a fault-injection hook,
+  // 1 + the local column group of CTA 0 whose copy is never issued (0: none, so that a
+  // zero-initialised ColArgs injects nothing)
+  uint64_t wait_ns;
+  int64_t stall_group_p1;
 };
 
 // Dense column-tile pass.  acc_f64 selects FP64 accumulation (else FP32).
@@ -293,6 +316,28 @@ cudaError_t launch_sketch_gather_csc(lp_dtype tv, const int64_t* colptr, const i
 // Q = G G^T (double-float, split along w); Gdf: 2 ldg w floats of work space (hi, lo of G)
 cudaError_t launch_gram(const double* G, float* Gdf, int ldg, int m, int w, int mp, double* Q,
                         double* Qsplit, int split, cudaStream_t st);
+cudaError_t launch_gram_df(const float* Gdf, int ldg, int m, int w, int mp, double* Q,
+                           double* Qsplit, int split, cudaStream_t st);
+// C = A B in double-float: A lower triangular, row-major planes (Ah, Al) with leading
+// dimension lda; B[k][j] = (Bh, Bl)[k sbk + j sbj] (b_lower: zero for k < j); C[i][j] written
+// at i sci + j scj, and optionally a second copy T at i sti + j stj.  i < M, j < N, k < K.
+struct TrmmArgs {
+  const float* Ah;
+  const float* Al;
+  int64_t lda;
+  const float* Bh;
+  const float* Bl;
+  int64_t sbk, sbj;
+  int M, N, K;
+  int b_lower;
+  float* Ch;
+  float* Cl;
+  int64_t sci, scj;
+  float* Th;
+  float* Tl;
+  int64_t sti, stj;
+};
+cudaError_t launch_df_trmm(const TrmmArgs& a, cudaStream_t st);
 cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double eps,
                              const double* v, cudaStream_t st);
 cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
@@ -317,6 +362,13 @@ cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* ro
 cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, double* z,
                              double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
                              cudaStream_t st);
+cudaError_t launch_precond_factored(const double* X, const double* XT, int mp, int m, int mode,
+                                    const double* r, double* t, double* z, double* sc, int* fl,
+                                    double* bpart, unsigned* bcnt, double rel_tol,
+                                    cudaStream_t st, const double* rold = nullptr,
+                                    const double* q = nullptr, const double* d = nullptr,
+                                    double* dy = nullptr, const double* qf = nullptr,
+                                    double* qzero = nullptr);
 cudaError_t symv_set_smem(int m);
 int coltile_max_grid(int num_sms);
 int csc_max_grid(int num_sms);

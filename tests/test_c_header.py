@@ -16,7 +16,8 @@ STRUCTS = {
                   "cg_batch", "inner_solver", "sketch_kind"],
     "lp_info": ["ipm_iters", "cg_iters_total", "cg_iters_last", "refine_steps", "rp_rel",
                 "rd_rel", "gap_rel", "mu", "obj", "alpha_max", "alpha", "f_norm", "v_norm",
-                "status", "f_target", "stream_dtype", "stream_switch_iter"],
+                "status", "f_target", "stream_dtype", "stream_switch_iter", "factor_two_stage",
+                "cg_precise_iter"],
     "lp_ipm_state": ["k", "stream_switch_iter", "r0", "mu0"],
 }
 
