@@ -30,8 +30,8 @@ if ROOT not in sys.path:
 
 # DRAM bytes of one CG product launch from an ncu capture of the same kernel source
 # (k_cgprod.cu at the recorded hash); reported only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha1": "17ef797053cfa0a86cda223fd6d4ce62827ca631",
-               "bytes_per_launch": 804.09e6,
+NCU_TRAFFIC = {"source_sha1": "6528766d8ab0ea89832ebfe8f8c83d75835a4310",
+               "bytes_per_launch": 803.96e6,
                "case": "dense m=1000 n=200000 FP32, ncu --set full (profiles/k_cgprod_cg_product_"
                        "dense_m1000_n200000_f32.md)"}
 
@@ -42,12 +42,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["dense", "sparse", "scaled", "serving", "svm"],
+    ap.add_argument("--workload", choices=["dense", "sparse", "scaled", "serving", "svm",
+                                           "matvec"],
                     default="dense",
                     help="dense: Gaussian m x n; sparse: CSR with --nnz-per-col nonzeros per "
                          "column; scaled: dense with column scales 10^U(-3,3); serving: a "
                          "Poisson stream of mixed dense/CSR LPs through the serving loop; svm: "
-                         "the l1-SVM LP on synthetic separable data with a Table 1 shape")
+                         "the l1-SVM LP on synthetic separable data with a Table 1 shape; "
+                         "matvec: the CG product A D^2 A^T v alone (one step = one product)")
     ap.add_argument("--svm-shape", choices=["arcene", "dexter", "drivface", "gene_rna"],
                     default="arcene")
     ap.add_argument("--sweep", action="store_true",
@@ -62,8 +64,16 @@ def parse_args():
                     help="serving: arrival rates in LP/s (comma separated, one run each)")
     ap.add_argument("--max-live", type=int, default=16, help="serving: concurrent instances")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: admission budget")
-    ap.add_argument("--plain-sample", type=int, default=32,
-                    help="serving: requests solved one at a time on the plain FP64 path")
+    ap.add_argument("--plain-sample", type=int, default=0,
+                    help="serving: requests solved one at a time on the plain FP64 path "
+                         "(0: all of them, the same requests as the batched path)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="dense: leave out the serving measurement of the default line")
+    ap.add_argument("--serving-requests", type=int, default=256,
+                    help="dense: requests of the serving measurement in the default line")
+    ap.add_argument("--serving-rates", type=str, default="16,2000",
+                    help="dense: arrival rates (LP/s) of the serving measurement, one below and "
+                         "one above saturation")
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--nnz-per-col", type=int, default=8)
@@ -73,6 +83,8 @@ def parse_args():
     ap.add_argument("--sketch", choices=["sparse", "gaussian"], default="sparse",
                     help="sparse sign sketch with --sketch-s nonzeros per row, or Gaussian")
     ap.add_argument("--cg-batch", type=int, default=4)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="host-driven CG loop instead of one CUDA graph launch per CG solve")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=20_000)
@@ -84,7 +96,7 @@ def parse_args():
         pts, feats = synth.SVM_SHAPES[args.svm_shape]
         args.m, args.n = pts, 2 * feats + 2 + pts
     defaults = {"dense": (1000, 200_000), "sparse": (5000, 2_000_000), "scaled": (2000, 500_000),
-                "serving": (512, 102_400), "svm": (args.m, args.n)}
+                "serving": (512, 102_400), "svm": (args.m, args.n), "matvec": (1000, 200_000)}
     dm, dn = defaults[args.workload]
     args.m = args.m or dm
     args.n = args.n or dn
@@ -279,26 +291,56 @@ def sample_lp(args):
     return lp, lp.A.astype(np.float64), ns
 
 
-def oracle_sample(args, iters_per_lp: float):
-    """Times the FP64 oracle's Algorithm 2 for a few iterations on a column sample of the
-    workload (same generator and m, n_s columns) and converts to LP/s of the full instance:
-    per-iteration time x (n / n_s) x IPM iterations per LP."""
+def oracle_run_record(args):
+    """The oracle's own end-to-end run of the full workload instance, stored by
+    tests/golden/make_oracle_run.py (IPM iterations, CG products, objective), or None."""
+    if args.workload != "dense" or args.sketch != "sparse":
+        return None
+    path = os.path.join(ROOT, "tests", "golden",
+                        f"oracle_run_dense_m{args.m}_n{args.n}_{args.dtype}_s{args.sketch_s}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+_FULL_LP = {}
+
+
+def oracle_sample(args, iters_per_lp: float, iters_source: str):
+    """Times the FP64 oracle's Algorithm 2 on the full workload instance itself (A as FP64):
+    its first --cpu-sample-iters IPM iterations, each with the sketch, QR factor, PCG and
+    correction at the real m and n.  LP/s = 1 / (time per iteration x IPM iterations per LP).
+    The first iterations need fewer CG iterations than the later ones, so this favours the
+    CPU.  Small workloads (the l1-SVM shapes) are solved to the end instead."""
     import numpy as np
 
-    import synth
     from oracle import iipm
 
-    lp, A, ns = sample_lp(args)
-    prm = iipm.Params(ipm_max_iter=args.cpu_sample_iters, sketch_s=args.sketch_s)
+    key = (args.workload, args.m, args.n, args.dtype, args.svm_shape)
+    if key not in _FULL_LP:
+        lp = make_lp(args)
+        A = lp.to_scipy() if args.workload == "sparse" else np.ascontiguousarray(lp.A, dtype=np.float64)
+        _FULL_LP.clear()
+        _FULL_LP[key] = (lp, A)
+    lp, A = _FULL_LP[key]
+    whole = args.workload == "svm"
+    prm = iipm.Params(ipm_max_iter=200 if whole else args.cpu_sample_iters,
+                      sketch_s=args.sketch_s,
+                      sketch_kind="gaussian" if args.sketch == "gaussian" else "sparse")
     t0 = time.perf_counter()
     r = iipm.ipm_solve(A, lp.b, lp.c, prm)
     dt = time.perf_counter() - t0
+    if whole:
+        return 1.0 / dt, (f"oracle Algorithm 2 (FP64 numpy/scipy) solving the whole instance "
+                          f"({r.iters} IPM iterations, {dt:.1f} s)"), dt
     per_iter = dt / max(r.iters, 1)
-    lp_s = 1.0 / (per_iter * (args.n / ns) * iters_per_lp)
-    sample = (f"oracle Algorithm 2 (FP64 numpy/scipy), first {r.iters} IPM iterations on the "
-              f"m={args.m}, n={ns} instance of the same generator ({dt:.1f} s); per-iteration "
-              f"time scaled by n/n_s = {args.n / ns:g} and by {iters_per_lp:g} IPM iterations "
-              f"per LP")
+    lp_s = 1.0 / (per_iter * iters_per_lp)
+    sample = (f"oracle Algorithm 2 (FP64 numpy/scipy) on the full m={args.m}, n={args.n} "
+              f"instance: its first {r.iters} IPM iterations ({r.cg_total} CG products, "
+              f"{dt:.1f} s), time per iteration x {iters_per_lp:g} IPM iterations per LP "
+              f"({iters_source})")
     return lp_s, sample, dt
 
 
@@ -322,6 +364,7 @@ def run_ours(args, rank, world, local):
     prm.sketch_s = args.sketch_s
     prm.sketch_kind = 1 if args.sketch == "gaussian" else 0
     prm.cg_batch = args.cg_batch
+    prm.use_graphs = 0 if args.no_graphs else 1
     sparse = args.workload == "sparse"
     sd = (args.dtype if not sparse else "f32") if args.stream == "same" else args.stream
     prm.stream_dtype = pkg.DTYPE_CODES[sd] if not sparse else pkg.LP_F64
@@ -346,9 +389,9 @@ def run_ours(args, rank, world, local):
     s = torch.empty(args.n, dtype=torch.float64, device=dev)
     for _ in range(args.warmup):
         info = pkg.lp_ipm_solve(ctx, x, y, s)
-    pkg.lp_profile_enable(ctx, True)
-    pkg.lp_profile_read(ctx, reset=True)
-    launches0 = pkg.lp_profile_read(ctx).launches
+    # the timed region runs without the library's event profiling
+    pkg.lp_profile_enable(ctx, False)
+    launches0 = pkg.lp_profile_read(ctx, reset=True).launches
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -364,8 +407,13 @@ def run_ours(args, rank, world, local):
     barrier(world)
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = pkg.lp_profile_read(ctx).launches - launches0
+    # one more solve, untimed, with CUDA events on the library's stream around every phase and
+    # every CG product: the per-launch duration of the CG product and the phase split
+    pkg.lp_profile_enable(ctx, True)
+    pkg.lp_profile_read(ctx, reset=True)
+    pkg.lp_ipm_solve(ctx, x, y, s)
     prof = pkg.lp_profile_read(ctx)
-    launches = prof.launches - launches0
     pkg.lp_profile_enable(ctx, False)
     obj = float(torch.dot(c_dev, x))
     pkg.lp_destroy(ctx)
@@ -407,8 +455,8 @@ def run_ours(args, rank, world, local):
     mv_avg_s = prof.matvec_ms / 1e3 / max(prof.matvec_count, 1)
     achieved = prof.matvec_bytes / mv_avg_s / 1e9 if prof.matvec_count else None
     traffic = None
-    if (not sparse and args.workload == "dense" and NCU_TRAFFIC["source_sha1"] == kernel_sha1()
-            and NCU_TRAFFIC["bytes_per_launch"]):
+    if (not sparse and args.workload == "dense" and (args.m, args.n, sd) == (1000, 200_000, "f32")
+            and NCU_TRAFFIC["source_sha1"] == kernel_sha1() and NCU_TRAFFIC["bytes_per_launch"]):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     ipm_iters = statistics.mean(i.ipm_iters for i in infos)
     cg_total = statistics.mean(i.cg_iters_total for i in infos)
@@ -435,6 +483,7 @@ def run_ours(args, rank, world, local):
             "tol": prm.tol, "sigma": prm.sigma, "gamma": prm.gamma,
             "l2": "inputs larger than L2 (A is %.0f MB)" % (a_bytes / 1e6),
             "parallelism": f"replicas x{world}",
+            "cg_loop": "host-driven" if args.no_graphs else "CUDA graph per CG solve",
         },
         "roofline": {
             "kernel": ("k_csc" if sparse else "k_cgprod") + " (CG product A D^2 A^T v)",
@@ -445,9 +494,16 @@ def run_ours(args, rank, world, local):
             "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic,
+            "traffic_source": (f"recorded constant: dram__bytes_read.sum + dram__bytes_write.sum "
+                               f"per launch from one ncu capture ({NCU_TRAFFIC['case']}) of the "
+                               f"same k_cgprod.cu source (sha1 {NCU_TRAFFIC['source_sha1'][:12]}); "
+                               "not a counter of this run") if traffic else None,
             "bytes_per_launch": prof.matvec_bytes,
             "avg_launch_us": 1e6 * mv_avg_s,
             "launches": int(prof.matvec_count),
+            "timing": "CUDA events on the library's stream around every CG product of one "
+                      "profiled LP solve run after the timed steps (the timed steps run without "
+                      "events)",
         },
         "e2e": {"value": (world * k_e2e / e2e_t) if k_e2e else None, "unit": "LP/s",
                 "h2d_bytes_per_step": h2d,
@@ -456,17 +512,49 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
         "ipm_iters_per_lp": ipm_iters,
         "cg_iters_per_lp": cg_total,
+        "cg_graph_solves_per_lp": statistics.mean(i.cg_graph_solves for i in infos),
         "objective": obj,
         "kkt": max(infos[-1].rp_rel, infos[-1].rd_rel, infos[-1].gap_rel),
-        "phase_ms_per_step": {k: v / args.steps for k, v in prof.as_dict()["phase_ms"].items()},
+        "phase_ms_per_lp": prof.as_dict()["phase_ms"],
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, sample, secs = oracle_sample(args, ipm_iters)
+        rec = oracle_run_record(args)
+        if rec:
+            it_lp, src = rec["ipm_iters"], "the oracle's own run of this instance (tests/golden)"
+        else:
+            it_lp, src = ipm_iters, "the GPU solve's count, which parity tests hold within one of the oracle's"
+        v, sample, secs = oracle_sample(args, it_lp, src)
         line["cpu_baseline"] = {"value": v, "unit": "LP/s", "cores": cpu_threads(),
                                 "kind": "oracle", "sample": sample}
+        if rec:
+            line["oracle_full_run"] = {k: rec[k] for k in ("ipm_iters", "cg_total", "objective",
+                                                            "kkt") if k in rec}
+            line["objective_rel_diff_vs_oracle"] = abs(obj - rec["objective"]) / abs(rec["objective"])
     else:
         line["cpu_baseline"] = None
+    if args.workload == "dense" and not args.no_serving and args.serving_requests > 0:
+        line["serving"] = serving_section(args, rank, world, local)
     return line
+
+
+def serving_section(args, rank, world, local):
+    """The serving half of the metric on the C5 request generator: the serving loop (BF16
+    stream, continuous batching) at one arrival rate below and one above saturation, and the
+    plain one-at-a-time FP64 path on the same requests."""
+    import numpy as np
+
+    reqs, insts = serving_instances(args.serving_requests)
+    rates = [float(r) for r in args.serving_rates.split(",")]
+    out = serving_measure(args, rank, world, local, rates, insts, reqs)
+    if rank != 0:
+        return None
+    runs, plain, comp = out
+    best = max(runs, key=lambda r: r["value"])
+    return {"metric": "serving LPs/s with p50/p99 latency, batched BF16 vs plain FP64",
+            "workload": serving_workload_name(len(insts)), "unit": "LP/s",
+            "value": best["value"], "runs": runs, "plain_fp64": plain,
+            "speedup_vs_plain_fp64": best["value"] / plain["value"], **comp,
+            "max_live": args.max_live, "budget_gb": args.budget_gb}
 
 
 # --------------------------------------------------------------------------- serving
@@ -497,21 +585,22 @@ def _submit(srv, pkg, kind, lp):
                       indices=lp.indices)
 
 
-def plain_fp64(pkg, insts, k):
-    """The first k requests one at a time on the plain path: A in FP64, FP64 stream, one
-    context per request, host buffers; returns (LP/s, objectives, seconds)."""
+def plain_fp64(pkg, insts, idx):
+    """The requests idx one at a time on the plain path: A in FP64, FP64 stream, one context
+    per request, host buffers; returns (LP/s, {i: objective}, seconds)."""
     import numpy as np
 
     prm = pkg.lp_params_default()
     data = []
-    for kind, lp in insts[:k]:
+    for i in idx:
+        kind, lp = insts[i]
         if kind == "dense":
-            data.append((kind, lp, np.ascontiguousarray(lp.At, dtype=np.float64)))
+            data.append((i, kind, lp, np.ascontiguousarray(lp.At, dtype=np.float64)))
         else:
-            data.append((kind, lp, lp.values.astype(np.float64)))
-    objs = []
+            data.append((i, kind, lp, lp.values.astype(np.float64)))
+    objs = {}
     t0 = time.perf_counter()
-    for kind, lp, vals in data:
+    for i, kind, lp, vals in data:
         x, y, s = np.empty(lp.n), np.empty(lp.m), np.empty(lp.n)
         if kind == "dense":
             ctx = pkg.lp_create(lp.m, lp.n, pkg.LP_DENSE_COLMAJOR, pkg.LP_F64, vals, None, None,
@@ -521,29 +610,26 @@ def plain_fp64(pkg, insts, k):
                                 lp.nnz, lp.b, lp.c, prm, None)
         pkg.lp_ipm_solve(ctx, x, y, s)
         pkg.lp_destroy(ctx)
-        objs.append(float(lp.c @ x))
+        objs[i] = float(lp.c @ x)
     secs = time.perf_counter() - t0
-    return k / secs, objs, secs
+    return len(idx) / secs, objs, secs
 
 
-def run_serving(args, rank, world, local):
+def serving_measure(args, rank, world, local, rates, insts, reqs):
+    """Serves the request stream at each arrival rate through the serving loop (batched, BF16
+    stream for dense requests), then solves the same requests one at a time on the plain FP64
+    path.  Returns (runs, plain, objective comparison) on rank 0."""
     import numpy as np
 
-    reqs, insts = serving_instances(args.requests)
-    import torch
-
     import paper_2003_08072_gb300 as pkg
+    import synth
 
-    pkg.load(build_if_missing=False)
-    torch.cuda.set_device(local)
     mine = shard(len(insts), rank, world)
     prm = pkg.lp_params_default()
     prm.stream_dtype = pkg.LP_BF16
     runs = []
     objs_batched, kkt_of = {}, {}
-    for rate in [float(r) for r in args.rate.split(",")]:
-        import synth
-
+    for rate in rates:
         arrivals = synth.poisson_arrivals(len(insts), rate)
         srv = pkg.LPServer(int(args.budget_gb * 2**30), max_live=args.max_live, params=prm)
         # warm-up: one request of each kind, untimed
@@ -587,7 +673,8 @@ def run_serving(args, rank, world, local):
             i = tickets[t]
             objs_batched[i] = float(insts[i][1].c @ r["x"])
             if r["status"] == 0:
-                kkt_of[i] = max(r["info"].rp_rel, r["info"].rd_rel, r["info"].gap_rel)
+                kkt_of[i] = max(kkt_of.get(i, 0.0), r["info"].rp_rel, r["info"].rd_rel,
+                                r["info"].gap_rel)
         runs.append({"rate": rate, "value": world * len(mine) / elapsed, "seconds": elapsed,
                      "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                     "p99": float(np.percentile(lat, 99)),
@@ -598,13 +685,35 @@ def run_serving(args, rank, world, local):
                      "mem_peak_gb": stats["mem_peak"] / 2**30, "clocks": clocks})
     if rank != 0:
         return None
-    k = min(args.plain_sample, len(insts))
-    plain_v, plain_objs, plain_s = plain_fp64(pkg, insts, k)
-    rel = [abs(objs_batched[i] - plain_objs[i]) / abs(plain_objs[i]) for i in range(k)
+    k = len(insts) if args.plain_sample <= 0 else min(args.plain_sample, len(insts))
+    plain_v, plain_objs, plain_s = plain_fp64(pkg, insts, list(range(k)))
+    rel = [abs(objs_batched[i] - plain_objs[i]) / abs(plain_objs[i]) for i in plain_objs
            if i in objs_batched]
-    # every request of the stream solved to the tolerance: scaled KKT of the returned iterate
-    kkt_max = max(kkt_of.values()) if kkt_of else None
-    best = runs[-1]
+    plain = {"value": plain_v, "unit": "LP/s", "seconds": plain_s,
+             "sample": (f"the same {k} requests" if k == len(insts) else f"the first {k} requests")
+             + " one at a time (FP64 A, FP64 stream, one context each, host buffers)"}
+    comp = {"max_rel_objective_diff_vs_plain": max(rel) if rel else None,
+            "max_scaled_kkt": max(kkt_of.values()) if kkt_of else None,
+            "same_requests": k == len(insts)}
+    return runs, plain, comp
+
+
+def run_serving(args, rank, world, local):
+    import numpy as np
+
+    reqs, insts = serving_instances(args.requests)
+    import torch
+
+    import paper_2003_08072_gb300 as pkg
+
+    pkg.load(build_if_missing=False)
+    torch.cuda.set_device(local)
+    rates = [float(r) for r in args.rate.split(",")]
+    out = serving_measure(args, rank, world, local, rates, insts, reqs)
+    if rank != 0:
+        return None
+    runs, plain, comp = out
+    best = max(runs, key=lambda r: r["value"])
     dense_elems = [m * n for kind, m, n, _ in reqs if kind == "dense"]
     return {
         "metric": "serving LPs/s (mixed dense FP32 / CSR 1% LP stream, Poisson arrivals)",
@@ -612,22 +721,23 @@ def run_serving(args, rank, world, local):
         "warmup": 2, "ms_per_step": 1e3 * best["seconds"] / len(insts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"{len(insts)} requests, m ~ U{{16..512}}, n = m U{{20..200}}, "
-                               "even requests dense Gaussian FP32, odd CSR at 1% density, "
-                               "Algorithm 2 to scaled KKT 1e-8 each",
+        "config": {"workload": serving_workload_name(len(insts)),
                    "mean_dense_elements": float(np.mean(dense_elems)),
                    "max_live": args.max_live, "budget_gb": args.budget_gb,
                    "stream_dtype": "bf16 (dense), f32 (CSR values)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": best["latency_ms"], "queued_ms": best["queued_ms"],
         "runs": runs,
-        "plain_fp64": {"value": plain_v, "unit": "LP/s", "sample": f"first {k} requests one at "
-                       "a time (FP64 A, FP64 stream, host buffers)", "seconds": plain_s},
-        "speedup_vs_plain_fp64": best["value"] / plain_v,
-        "max_rel_objective_diff_vs_plain": max(rel) if rel else None,
-        "max_scaled_kkt": kkt_max,
+        "plain_fp64": plain,
+        "speedup_vs_plain_fp64": best["value"] / plain["value"],
+        **comp,
         "clocks": best["clocks"],
     }
+
+
+def serving_workload_name(count):
+    return (f"{count} requests, m ~ U{{16..512}}, n = m U{{20..200}}, even requests dense "
+            "Gaussian FP32, odd CSR at 1% density, Algorithm 2 to scaled KKT 1e-8 each")
 
 
 # --------------------------------------------------------------------------- (w, tolCG) sweep
@@ -780,30 +890,33 @@ def run_sketch_study(args, rank, world, local):
 
 # --------------------------------------------------------------------------- reference arm
 
-def oracle_iters_per_lp(args) -> float:
-    """IPM iterations the oracle needs for the column-sample instance (exact-solve variant,
-    cheap; the sketch variant agrees to within one iteration)."""
+def oracle_iters_per_lp(args):
+    """IPM iterations per LP for the reference arm: the oracle's own run of this instance
+    (tests/golden), else the oracle solving a column sample of it to the end (a stand-in for
+    workloads without a stored run)."""
     import numpy as np
 
-    import synth
     from oracle import iipm
 
+    rec = oracle_run_record(args)
+    if rec:
+        return float(rec["ipm_iters"]), "the oracle's own run of this instance (tests/golden)"
     lp, A, ns = sample_lp(args)
-    r = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(), variant="exact")
-    return float(r.iters)
+    r = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(sketch_s=args.sketch_s))
+    return float(r.iters), f"the oracle's run of the n={ns} column sample of this instance"
 
 
 def run_reference(args, rank, world):
     """The FP64 oracle, as it stands, on the host cores: each step one bounded sample."""
     if rank != 0:
         return None
-    iters_per_lp = oracle_iters_per_lp(args)
+    iters_per_lp, src = oracle_iters_per_lp(args)
     for _ in range(args.warmup):
-        oracle_sample(args, iters_per_lp)
+        oracle_sample(args, iters_per_lp, src)
     vals, secs = [], 0.0
     sample = ""
     for _ in range(args.steps):
-        v, sample, dt = oracle_sample(args, iters_per_lp)
+        v, sample, dt = oracle_sample(args, iters_per_lp, src)
         vals.append(v)
         secs += dt
     value = statistics.mean(vals)
@@ -821,6 +934,67 @@ def run_reference(args, rank, world):
     }
 
 
+def run_matvec(args, rank, world, local):
+    """The PCG matvec alone: y = A D^2 A^T v through lp_normal_matvec on the streamed copy
+    (the staged product k_cgprod plus the reduction of its partial sums), A resident in HBM
+    and larger than L2.  value = algorithmic GB/s (m n b_A + 4 n + 16 m bytes per product)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2003_08072_gb300 as pkg
+
+    pkg.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lp = synth.dense_lp(0, args.m, args.n, dtype=np.float32)
+    sd = "f32" if args.stream == "same" else args.stream
+    prm = pkg.lp_params_default()
+    prm.stream_dtype = pkg.DTYPE_CODES[sd]
+    stream = torch.cuda.current_stream(dev)
+    At = torch.from_numpy(lp.At).to(dev)
+    ctx = pkg.lp_create(args.m, args.n, pkg.LP_DENSE_COLMAJOR, pkg.LP_F32, At, None, None, 0,
+                        torch.from_numpy(lp.b).to(dev), torch.from_numpy(lp.c).to(dev), prm,
+                        stream.cuda_stream)
+    del At
+    x, _, s = synth.iterate_point(1, args.m, args.n, spread=2.0)
+    d2 = torch.from_numpy(x / s).to(dev)
+    v = torch.from_numpy(np.random.default_rng(2).standard_normal(args.m)).to(dev)
+    y = torch.empty(args.m, dtype=torch.float64, device=dev)
+    code = pkg.DTYPE_CODES[sd]
+    for _ in range(args.warmup):
+        pkg.lp_normal_matvec(ctx, d2, v, y, None, code)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        pkg.lp_normal_matvec(ctx, d2, v, y, None, code)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
+    pkg.lp_destroy(ctx)
+    esz = {"f32": 4, "bf16": 2, "f16": 2}[sd]
+    nbytes = args.m * args.n * esz + 4 * args.n + 16 * args.m
+    if rank != 0:
+        return None
+    peak, kind = read_peaks()
+    gbs = world * args.steps * nbytes / t / 1e9
+    return {"metric": f"PCG matvec HBM GB/s (A D^2 A^T v, dense m={args.m} n={args.n}, "
+                      f"A streamed {sd.upper()})",
+            "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": sd,
+            "data": "synthetic",
+            "config": {"workload": f"A D^2 A^T v, Gaussian A m={args.m} n={args.n}",
+                       "l2": f"inputs larger than L2 (A is {args.m * args.n * esz / 1e6:.0f} MB)",
+                       "bytes_per_product": nbytes},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak,
+                         "peak_kind": f"{kind} hbm_gbs", "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": None}}
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_setup()
@@ -828,6 +1002,8 @@ def main():
         line = run_reference(args, rank, world)
     elif args.workload == "serving":
         line = run_serving(args, rank, world, local)
+    elif args.workload == "matvec":
+        line = run_matvec(args, rank, world, local)
     elif args.workload == "svm" and args.sweep:
         line = run_sweep(args, rank, world, local)
     elif args.sketch_study and args.workload in ("dense", "svm"):

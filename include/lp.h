@@ -90,6 +90,11 @@ typedef struct {
                             LP_SKETCH_GAUSSIAN (1): W with N(0, 1/w) entries (Sec. 5, the sketch of the
                             experiments, Sec. 6), dense A only; forming A D W costs 2 m n w, meant for
                             the small LPs of the experiments (0) */
+  int32_t use_graphs;    /* 1: after a context's first CG solve, each CG solve runs as one CUDA graph
+                            launch whose WHILE node repeats the CG iteration on the device until the
+                            stop rule holds (no host round trip per cg_batch); 0: every CG iteration
+                            is enqueued by the host and the stop flag read every cg_batch
+                            iterations.  Profiling (lp_profile_enable) runs the host-driven loop (1) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */
@@ -113,6 +118,8 @@ typedef struct {
   int32_t cg_precise_iter;    /* IPM iteration from which the CG products accumulated in FP64-class
                                  arithmetic over the master copy, because FP64 refinement of FP32
                                  products stopped contracting on the master copy itself; -1 if never */
+  int32_t cg_graph_solves;    /* CG solves of this call that ran as one CUDA graph launch each
+                                 (lp_params.use_graphs) */
 } lp_info;
 
 /* Fills *prm with the defaults listed above.  LP_ERR_ARG if prm is NULL. */

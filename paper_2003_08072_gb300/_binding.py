@@ -40,6 +40,7 @@ class lp_params(ctypes.Structure):
         ("cg_batch", ctypes.c_int32),
         ("inner_solver", ctypes.c_int32),
         ("sketch_kind", ctypes.c_int32),
+        ("use_graphs", ctypes.c_int32),
     ]
 
 
@@ -64,6 +65,7 @@ class lp_info(ctypes.Structure):
         ("stream_switch_iter", ctypes.c_int32),
         ("factor_two_stage", ctypes.c_int32),
         ("cg_precise_iter", ctypes.c_int32),
+        ("cg_graph_solves", ctypes.c_int32),
     ]
 
     def as_dict(self):

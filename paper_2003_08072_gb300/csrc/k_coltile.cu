@@ -229,10 +229,7 @@ int launch_t(ColArgs a, int num_sms, cudaStream_t st) {
       default: kern = k_coltile<TA, ACC, 8, 2, MODE>; break;
     }
   }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  int per_sm = occupancy_cached((const void*)kern, threads, 0);
   if (per_sm > 8) per_sm = 8;
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > a.ntiles) grid = a.ntiles;
@@ -308,10 +305,7 @@ int launch_capped_t(ColArgs a, int num_sms, int max_grid, cudaStream_t st) {
       default: kern = k_coltile<TA, ACC, 8, 2, MODE_NORMAL>; break;
     }
   }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  int per_sm = occupancy_cached((const void*)kern, threads, 0);
   if (per_sm > 8) per_sm = 8;
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > max_grid) grid = max_grid;

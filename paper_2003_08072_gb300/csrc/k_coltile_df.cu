@@ -220,10 +220,7 @@ int launch_df_t(ColArgs a, int num_sms, cudaStream_t st) {
     case 2: kern = k_coltile_df<2, 4, MODE>; break;
     default: kern = k_coltile_df<4, 2, MODE>; break;
   }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  int per_sm = occupancy_cached((const void*)kern, threads, 0);
   if (per_sm > 8) per_sm = 8;
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > a.ntiles) grid = a.ntiles;

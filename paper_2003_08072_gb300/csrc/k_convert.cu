@@ -1,5 +1,7 @@
 // Layout and precision conversion of the input matrix, finiteness checks, scalar setters.
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <unordered_map>
 
 #include "dev_util.cuh"
@@ -200,6 +202,26 @@ cudaError_t launch_apply_W(const int32_t* hb, int ss, const double* u, int64_t n
 // kernel concurrently with a larger need, and lowering the limit between their attribute call
 // and their launch would make that launch fail.  The limit is raised for any size (not only
 // above 48 KB): the 48 KB default covers static plus dynamic shared memory together.
+// Resident CTAs per SM of a kernel at a block size and dynamic shared memory, queried once
+// per (kernel, threads, smem) and cached: the launchers are also recorded into CUDA graphs,
+// where nothing but the launches themselves should reach the runtime.
+int occupancy_cached(const void* func, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(func, threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 0;
+  }
+  if (per_sm < 1) per_sm = 1;
+  cache[key] = per_sm;
+  return per_sm;
+}
+
 cudaError_t ensure_dyn_smem(const void* func, size_t bytes) {
   static std::mutex mu;
   static std::unordered_map<const void*, size_t> set;

@@ -81,10 +81,7 @@ static int launch_csc_t(CscArgs a, int num_sms, cudaStream_t st) {
   if (smem > 220 * 1024) return -1;
   auto kern = k_csc<TV, ACC, MODE>;
   if (ensure_dyn_smem((const void*)kern, smem) != cudaSuccess) return -1;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  int per_sm = occupancy_cached((const void*)kern, 512, smem);
   if (per_sm > 2) per_sm = 2;
   int64_t grid = (int64_t)num_sms * per_sm;
   const int64_t need = (a.n + 63) / 64;

@@ -342,6 +342,17 @@ cudaError_t launch_precond_factored(const double* X, const double* XT, int mp, i
   return cudaGetLastError();
 }
 
+__global__ void k_cg_cond(cudaGraphConditionalHandle h, int* fl, int max_trips) {
+  const int trips = fl[FL_TRIPS] + 1;
+  fl[FL_TRIPS] = trips;
+  cudaGraphSetConditional(h, (fl[FL_DONE] == 0 && trips < max_trips) ? 1u : 0u);
+}
+
+cudaError_t launch_cg_cond(cudaGraphConditionalHandle h, int* fl, int max_trips, cudaStream_t st) {
+  { note_launch(); k_cg_cond<<<1, 1, 0, st>>>(h, fl, max_trips); }
+  return cudaGetLastError();
+}
+
 cudaError_t symv_set_smem(int m) {
   const int bytes = ((m + 3) & ~3) * 2 * (int)sizeof(double);
   cudaError_t e = ensure_dyn_smem((const void*)k_symv<true>, bytes);

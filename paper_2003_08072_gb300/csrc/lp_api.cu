@@ -1,6 +1,8 @@
 // C ABI of the sketch-preconditioned infeasible IPM (include/lp.h): context management and
 // the host-side sequencing of the kernels for Algorithms 1 and 2.
 #include <math.h>
+#include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <memory>
@@ -83,6 +85,7 @@ lp_status lp_params_default(lp_params* p) {
   p->cg_batch = 4;
   p->inner_solver = LP_INNER_CG;
   p->sketch_kind = LP_SKETCH_SPARSE;
+  p->use_graphs = 1;
   return LP_OK;
 }
 
@@ -178,6 +181,8 @@ static void dfree(void* p) {
   if (p) cudaFreeAsync(p, t_alloc_stream);
 }
 
+static void cg_graph_free(lp_ctx::CgGraph& g);
+
 extern "C" void lp_destroy(lp_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
@@ -205,6 +210,8 @@ extern "C" void lp_destroy(lp_ctx* c) {
     if (pr.b) cudaEventDestroy(pr.b);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& g : c->cg_graphs) cg_graph_free(g);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   delete c;
 }
 
@@ -966,6 +973,163 @@ static lp_status precond_cg_step(lp_ctx* c, const double* rold, const double* q,
   return LP_OK;
 }
 
+// One CG loop's operands: iteration j forms d_j = z + beta d_{j-1} into d[j & 1], the product
+// q = K d_j (into q[j & 1] for the atomically reduced FP32 product) and r_{j+1} into r[(j+1) & 1].
+struct CgLoop {
+  int op;          // 0: K = A D^2 A^T; 1: K = G G^T (the correction's PCG on Q)
+  double* delta;   // the solution accumulates here
+  bool atomic_q;
+  double* r[2];
+  double* d[2];
+  double* q[2];
+};
+
+static lp_status cg_iteration(lp_ctx* c, const CgLoop& L, int j, bool record_mv) {
+  double* dnew = L.d[j & 1];
+  const double* dold = L.d[(j + 1) & 1];
+  if (L.op == 0)
+    LP_TRY(pass_normal(c, c->cg_precise, nullptr, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1,
+                       record_mv, c->z, dold, dnew, L.atomic_q ? L.q[j & 1] : nullptr));
+  else
+    LP_TRY(pass_gram(c, c->G, nullptr, nullptr, c->q, nullptr, RED_CG_Q, 1, c->z, dold, dnew));
+  LP_TRY(precond_cg_step(c, L.r[j & 1], c->q, dnew, L.delta, L.r[(j + 1) & 1], c->z,
+                         L.atomic_q ? L.q[j & 1] : nullptr,
+                         L.atomic_q ? L.q[(j + 1) & 1] : nullptr));
+  return LP_OK;
+}
+
+// Everything the captured kernels bake in: the loop's operands and the context state that
+// selects kernels and matrices.
+struct CgGraphKey {
+  int op, atomic_q, precise, factored, use_staged, s_dtype, lda_s, max_trips;
+  const void* delta;
+  const void* As;
+  const void* svals;
+};
+
+static void cg_graph_free(lp_ctx::CgGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  g.exec = nullptr;
+  g.graph = nullptr;
+}
+
+// Builds the graph of a CG loop: a WHILE node whose body runs iterations 0 and 1 (so the
+// buffers' parity is the same at every entry) and then the condition kernel.  The kernels of a
+// finished solve return at once, so a solve that stops after an even iteration is exact.
+static lp_status cg_graph_build(lp_ctx* c, const CgLoop& L, int max_trips, cudaGraph_t* out) {
+  *out = nullptr;
+  if (!c->cap_st) LP_CU(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+  // the launchers enqueue on c->st: point it at the private stream while recording
+  struct StreamSwap {
+    lp_ctx* c;
+    cudaStream_t saved;
+    ~StreamSwap() { c->st = saved; }
+  } swap{c, c->st};
+  c->st = c->cap_st;
+  cudaGraph_t g = nullptr;
+  LP_CU(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(c->st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return lp_cuda_fail(e, "CG loop graph");
+  }
+  lp_status st = cg_iteration(c, L, 0, false);
+  if (st == LP_OK) st = cg_iteration(c, L, 1, false);
+  if (st == LP_OK) {
+    const cudaError_t e2 = launch_cg_cond(h, c->fl, max_trips, c->st);
+    if (e2 != cudaSuccess) st = lp_cuda_fail(e2, "CG loop condition");
+  }
+  cudaGraph_t body = nullptr;
+  const cudaError_t e3 = cudaStreamEndCapture(c->st, &body);
+  if (st == LP_OK && e3 != cudaSuccess) st = lp_cuda_fail(e3, "CG loop capture");
+  if (st != LP_OK) {
+    cudaGraphDestroy(g);
+    return st;
+  }
+  *out = g;
+  return LP_OK;
+}
+
+// Graphs given up: say why once per process (the host-driven loop gives the same results).
+static void graph_warn(const lp_ctx* c) {
+  static std::atomic<bool> said{false};
+  if (!said.exchange(true))
+    fprintf(stderr, "lp_gb300: CUDA graphs of the CG loop unavailable (%s); running the "
+                    "host-driven loop\n", c->graph_error.c_str());
+}
+
+// Runs the CG loop of L as one graph launch (building and caching its graph on first use).
+// *ran is false when graphs are unavailable here; the caller then runs the host-driven loop.
+static lp_status cg_graph_launch(lp_ctx* c, const CgLoop& L, int max_iter, bool* ran) {
+  *ran = false;
+  CgGraphKey k{};
+  k.op = L.op;
+  k.atomic_q = L.atomic_q;
+  k.precise = c->cg_precise;
+  k.factored = c->factored;
+  k.use_staged = c->use_staged;
+  k.s_dtype = (int)c->s_dtype;
+  k.lda_s = c->lda_s;
+  k.max_trips = max_iter / 2 + 2;
+  k.delta = L.delta;
+  k.As = c->As;
+  k.svals = c->svals;
+  static_assert(sizeof(CgGraphKey) <= sizeof(lp_ctx::CgGraph::key), "graph key size");
+  unsigned char key[sizeof(lp_ctx::CgGraph::key)] = {};
+  memcpy(key, &k, sizeof(k));
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : c->cg_graphs)
+    if (memcmp(g.key, key, sizeof(key)) == 0) exec = g.exec;
+  if (!exec) {
+    cudaGraph_t g = nullptr;
+    if (cg_graph_build(c, L, k.max_trips, &g) != LP_OK) {
+      // graphs unavailable (e.g. a driver without conditional nodes): stay eager
+      c->graph_error = lp_last_error();
+      cudaGetLastError();
+      c->use_graphs = false;
+      graph_warn(c);
+      return LP_OK;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    if (ei != cudaSuccess) {
+      c->graph_error = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+      cudaGetLastError();
+      cudaGraphDestroy(g);
+      c->use_graphs = false;
+      graph_warn(c);
+      return LP_OK;
+    }
+    if (c->cg_graphs.size() >= 8) {
+      cg_graph_free(c->cg_graphs.front());
+      c->cg_graphs.erase(c->cg_graphs.begin());
+    }
+    lp_ctx::CgGraph cg{};
+    memcpy(cg.key, key, sizeof(key));
+    cg.graph = g;
+    cg.exec = ex;
+    c->cg_graphs.push_back(cg);
+    exec = ex;
+  }
+  LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_TRIPS, 0, c->st));
+  LP_CU(cudaGraphLaunch(exec, c->st));
+  ++c->graph_launches;
+  *ran = true;
+  return LP_OK;
+}
+
 // PCG from delta = 0 with preconditioner M = Q^{-1} (Alg. 1 step 3), stopping when
 // rho_j = r_j^T M r_j <= min(rel^2 rho_0, abs_thr^2) or after max_iter products.
 //   op 0: (A D^2 A^T) delta = rhs with A streamed in the context's stream dtype;
@@ -995,22 +1159,25 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
   const bool atomic_q = (op == 0) && !c->sparse && c->s_dtype != LP_F64 && !c->cg_precise;
   double* qbuf[2] = {c->qf, c->qf + (size_t)kQCopies * m};
   if (atomic_q) LP_CU(cudaMemsetAsync(c->qf, 0, (size_t)kQCopies * m * sizeof(double), c->st));
+  CgLoop L{op, delta, atomic_q, {rbuf[0], rbuf[1]}, {dbuf[0], dbuf[1]}, {qbuf[0], qbuf[1]}};
+  // the device-side loop (one graph launch per solve) once this context has run a CG solve
+  // eagerly, with no profiling events or fault injection to honour
+  bool finished = false;
+  if (c->use_graphs && c->prm.use_graphs && c->cg_solves > 0 && !c->prof_on &&
+      c->stall_group_p1 == 0) {
+    bool built = false;
+    LP_TRY(cg_graph_launch(c, L, max_iter, &built));
+    if (built) {
+      LP_TRY(sync_scalars(c));
+      finished = c->fl_h[FL_DONE] != 0;
+    }
+  }
+  ++c->cg_solves;
+  // host-driven loop: cg_batch iterations enqueued per check of the stop flag
   int done_before = 0;
   int j = 0;
-  for (;;) {
-    for (int b = 0; b < c->prm.cg_batch; ++b, ++j) {
-      double* dnew = dbuf[j & 1];
-      const double* dold = dbuf[(j + 1) & 1];
-      if (op == 0)
-        LP_TRY(pass_normal(c, c->cg_precise, nullptr, c->d2, nullptr, RED_CG_Q, c->q, nullptr, 1,
-                           true, c->z, dold, dnew, atomic_q ? qbuf[j & 1] : nullptr));
-      else
-        LP_TRY(pass_gram(c, c->G, nullptr, nullptr, c->q, nullptr, RED_CG_Q, 1, c->z, dold,
-                         dnew));
-      LP_TRY(precond_cg_step(c, rbuf[j & 1], c->q, dnew, delta, rbuf[(j + 1) & 1], c->z,
-                             atomic_q ? qbuf[j & 1] : nullptr,
-                             atomic_q ? qbuf[(j + 1) & 1] : nullptr));
-    }
+  while (!finished) {
+    for (int b = 0; b < c->prm.cg_batch; ++b, ++j) LP_TRY(cg_iteration(c, L, j, true));
     LP_TRY(sync_scalars(c));
     if (!c->mv_pending.empty()) prof_harvest_mv(c, c->fl_h[FL_ITERS] - done_before);
     done_before = c->fl_h[FL_ITERS];
@@ -1147,6 +1314,7 @@ static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_
   const int m = c->m;
   const int64_t n = c->n;
   lp_info inf{};
+  const long long graphs0 = c->graph_launches;
   if (resume && resume->stream_switch_iter >= 0) stream_switch(c, resume->stream_switch_iter);
   if (start_given) {
     LP_CU(cudaMemcpyAsync(c->x, x, n * sizeof(double), cudaMemcpyDefault, c->st));
@@ -1231,6 +1399,7 @@ static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_
   inf.stream_dtype = c->s_dtype;
   inf.stream_switch_iter = c->switch_iter;
   inf.cg_precise_iter = c->precise_iter;
+  inf.cg_graph_solves = (int32_t)(c->graph_launches - graphs0);
   c->ipm_state.k = k;
   c->ipm_state.stream_switch_iter = c->switch_iter;
   c->ipm_state.r0 = r0;
@@ -1272,6 +1441,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
   if (!c || !x || !s || !p || !dy) return fail(LP_ERR_ARG, "lp_normal_solve: NULL argument");
   if (k < 0) return fail(LP_ERR_ARG, "lp_normal_solve: k < 0");
   stream_reset(c);
+  const long long graphs0 = c->graph_launches;
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
                             c->c, c->st, c->d2f, stream_cs2(c)));
   LP_TRY(sync_scalars(c));
@@ -1303,6 +1473,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
     inf.stream_switch_iter = c->switch_iter;
     inf.factor_two_stage = c->factor_stages == 2 ? 1 : 0;
     inf.cg_precise_iter = c->precise_iter;
+    inf.cg_graph_solves = (int32_t)(c->graph_launches - graphs0);
     *info = inf;
   }
   return LP_OK;

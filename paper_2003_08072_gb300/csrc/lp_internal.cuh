@@ -51,7 +51,8 @@ enum Flag {
   FL_TIMEOUT,    // a bounded wait in a kernel gave up
   FL_RICH,       // the running solve is Richardson's iteration (App. A): alpha = 1, beta = 0
   FL_DIVERGED,   // Richardson's residual grew past 1e6 times its start
-  FL_COUNT = 8
+  FL_TRIPS,      // bodies run by the device-side CG loop of the current graph launch
+  FL_COUNT = 16
 };
 
 extern std::atomic<long long> g_launches;   // kernel launches issued (lp_api.cu)
@@ -168,6 +169,22 @@ struct lp_ctx {
   void* pin_blk = nullptr;     // pinned host block holding sc_h and fl_h
   double* sc_h = nullptr;      // pinned host mirror of sc
   int* fl_h = nullptr;         // pinned host mirror of fl
+
+  // CUDA graphs of the CG loop: one WHILE node whose body is two CG iterations and a
+  // condition kernel, so a whole CG solve is one graph launch with no host round trip; built
+  // per configuration of the loop (operator, copy streamed, preconditioner form, ...)
+  struct CgGraph {
+    unsigned char key[128];
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+  };
+  bool use_graphs = true;      // lp_params.use_graphs and no failure so far
+  cudaStream_t cap_st = nullptr;   // private stream the graphs are recorded on (the context
+                                   // stream may be the legacy default stream, which cannot be)
+  std::string graph_error;     // why graphs were given up, if they were
+  long long cg_solves = 0;     // CG solves run (the first one always runs eagerly)
+  std::vector<CgGraph> cg_graphs;
+  long long graph_launches = 0;
 
   // profiling (CUDA events on st)
   struct EvPair {
@@ -362,6 +379,9 @@ cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* ro
 cudaError_t launch_symv_init(const double* M, int mp, int m, const double* r, double* z,
                              double* sc, int* fl, double* bpart, unsigned* bcnt, double rel_tol,
                              cudaStream_t st);
+// Condition of the device-side CG loop: continue while the solve is unfinished and the body
+// has run fewer than max_trips times (a CUDA graph WHILE node's handle).
+cudaError_t launch_cg_cond(cudaGraphConditionalHandle h, int* fl, int max_trips, cudaStream_t st);
 cudaError_t launch_precond_factored(const double* X, const double* XT, int mp, int m, int mode,
                                     const double* r, double* t, double* z, double* sc, int* fl,
                                     double* bpart, unsigned* bcnt, double rel_tol,
@@ -408,6 +428,7 @@ cudaError_t launch_sketch_gauss(lp_dtype ta, const void* A, int64_t lda, int m, 
                                 cudaStream_t st);
 cudaError_t launch_apply_W_gauss(uint64_t seed, int k, int64_t n, int w, const double* u, double* wu,
                                  cudaStream_t st);
+int occupancy_cached(const void* func, int threads, size_t smem);
 // Raises (never lowers) a kernel's dynamic shared-memory limit to at least `bytes`.
 cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
 cudaError_t launch_convert_colscaled(const void* src, lp_dtype sdt, int lda, int m, int64_t n,

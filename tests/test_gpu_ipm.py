@@ -187,3 +187,34 @@ def test_iteration_cap_reports_not_converged():
     assert info.status == pkg._binding.LP_ERR_NOT_CONVERGED
     assert info.ipm_iters == 3
     assert np.isfinite(x.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("case", ["dense_f64", "dense_f32", "dense_bf16", "sparse", "countsketch"])
+def test_graph_captured_cg_matches_eager(case):
+    """The device-side CG loop (one CUDA graph launch per CG solve) against the host-driven
+    loop: same IPM iteration count within one, same objective to 1e-6, both to scaled KKT
+    1e-8; the captured run really ran its CG solves as graphs."""
+    import paper_2003_08072_gb300 as pkg
+
+    out = {}
+    for graphs in (1, 0):
+        if case == "sparse":
+            lp = synth.sparse_lp(1, 60, 5000, nnz_per_col=6)
+            prm = params(use_graphs=graphs)
+            s = pkg.LPSolver.csr(lp.m, lp.n, T(lp.indptr), T(lp.indices), T(lp.values), T(lp.b),
+                                 T(lp.c), params=prm)
+        else:
+            dt = np.float64 if case == "dense_f64" or case == "countsketch" else np.float32
+            lp = synth.dense_lp(3, 80, 6000, dtype=dt)
+            prm = params(use_graphs=graphs, sketch_s=1 if case == "countsketch" else 4,
+                         stream_dtype=pkg.LP_BF16 if case == "dense_bf16" else pkg.LP_F64)
+            s = pkg.LPSolver.dense(T(lp.At), T(lp.b), T(lp.c), params=prm)
+        x, y, sv, info = s.solve()
+        out[graphs] = (float(lp.c @ x.cpu().numpy()), info)
+        s.close()
+    (og, ig), (oe, ie) = out[1], out[0]
+    assert ig.status == 0 and ie.status == 0
+    assert ig.cg_graph_solves > 0 and ie.cg_graph_solves == 0
+    assert abs(ig.ipm_iters - ie.ipm_iters) <= 1
+    assert abs(og - oe) <= 1e-6 * abs(oe)
+    assert max(ig.rp_rel, ig.rd_rel, ig.gap_rel) <= 1e-8
