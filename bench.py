@@ -83,6 +83,9 @@ def parse_args():
     ap.add_argument("--sketch", choices=["sparse", "gaussian"], default="sparse",
                     help="sparse sign sketch with --sketch-s nonzeros per row, or Gaussian")
     ap.add_argument("--cg-batch", type=int, default=4)
+    ap.add_argument("--no-gram-tc", action="store_true",
+                    help="Gram product of the factor in double-float on the FP32 pipes instead "
+                         "of the tensor cores")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven CG loop instead of one CUDA graph launch per CG solve")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -365,6 +368,7 @@ def run_ours(args, rank, world, local):
     prm.sketch_kind = 1 if args.sketch == "gaussian" else 0
     prm.cg_batch = args.cg_batch
     prm.use_graphs = 0 if args.no_graphs else 1
+    prm.gram_tensor_cores = 0 if args.no_gram_tc else 1
     sparse = args.workload == "sparse"
     sd = (args.dtype if not sparse else "f32") if args.stream == "same" else args.stream
     prm.stream_dtype = pkg.DTYPE_CODES[sd] if not sparse else pkg.LP_F64
@@ -484,6 +488,8 @@ def run_ours(args, rank, world, local):
             "l2": "inputs larger than L2 (A is %.0f MB)" % (a_bytes / 1e6),
             "parallelism": f"replicas x{world}",
             "cg_loop": "host-driven" if args.no_graphs else "CUDA graph per CG solve",
+            "gram": ("double-float, FP32 pipes" if args.no_gram_tc else
+                     "tensor cores (tcgen05, exact BF16 digit slices)"),
         },
         "roofline": {
             "kernel": ("k_csc" if sparse else "k_cgprod") + " (CG product A D^2 A^T v)",

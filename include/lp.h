@@ -95,6 +95,10 @@ typedef struct {
                             stop rule holds (no host round trip per cg_batch); 0: every CG iteration
                             is enqueued by the host and the stop flag read every cg_batch
                             iterations.  Profiling (lp_profile_enable) runs the host-driven loop (1) */
+  int32_t gram_tensor_cores; /* 1: the Gram product Q = (A D W)(A D W)^T of the factor runs on the tensor
+                            cores (tcgen05), made exact by splitting each row of the sketch into eight
+                            BF16 digit slices of 6 bits (accurate to ~2^-48 of |G_i| |G_j| w, as the
+                            double-float product); 0: double-float product on the FP32 pipes (1) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */

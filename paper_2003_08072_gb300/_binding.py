@@ -41,6 +41,7 @@ class lp_params(ctypes.Structure):
         ("inner_solver", ctypes.c_int32),
         ("sketch_kind", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
+        ("gram_tensor_cores", ctypes.c_int32),
     ]
 
 

@@ -152,10 +152,15 @@ int gram_split(int m, int w, int num_sms) {
   return best;
 }
 
+cudaError_t launch_split_df(const double* G, size_t count, float* Gdf, cudaStream_t st) {
+  { note_launch(); k_split_df<<<2048, 256, 0, st>>>(G, count, Gdf, Gdf + count); }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gram(const double* G, float* Gdf, int ldg, int m, int w, int mp, double* Q,
                         double* Qsplit, int split, cudaStream_t st) {
-  const size_t count = (size_t)ldg * w;
-  { note_launch(); k_split_df<<<2048, 256, 0, st>>>(G, count, Gdf, Gdf + count); }
+  const cudaError_t e = launch_split_df(G, (size_t)ldg * w, Gdf, st);
+  if (e != cudaSuccess) return e;
   return launch_gram_df(Gdf, ldg, m, w, mp, Q, Qsplit, split, st);
 }
 

@@ -86,6 +86,7 @@ lp_status lp_params_default(lp_params* p) {
   p->inner_solver = LP_INNER_CG;
   p->sketch_kind = LP_SKETCH_SPARSE;
   p->use_graphs = 1;
+  p->gram_tensor_cores = 1;
   return LP_OK;
 }
 
@@ -198,7 +199,8 @@ extern "C" void lp_destroy(lp_ctx* c) {
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
-                  c->bcnt, c->X1, c->XF, c->XFT, c->G1df, c->ptmp};
+                  c->bcnt, c->X1, c->XF, c->XFT, c->G1df, c->ptmp, c->gdig, c->gex,
+                  c->gpart};
   for (void* p : bufs) dfree(p);
   pinned_release(c->pin_blk);
   for (auto& pr : c->ev_pending) {
@@ -251,6 +253,10 @@ static lp_status alloc_workspace(lp_ctx* c) {
   c->qsplit = gram_split(m, c->w, c->num_sms);
   const int nt = c->mp / 64;
   LP_TRY(dalloc(&c->Qsplit, (size_t)c->qsplit * (nt * (nt + 1) / 2) * 64 * 64));
+  // tensor-core Gram product (digits are rewritten completely by every product)
+  LP_TRY(dalloc((unsigned char**)&c->gdig, gram_tc_digit_bytes(m, c->w)));
+  LP_TRY(dalloc(&c->gex, (size_t)gram_tc_rows(m)));
+  LP_TRY(dalloc((unsigned char**)&c->gpart, gram_tc_part_bytes(m, c->mp, c->w, c->num_sms)));
   // scalars
   LP_TRY(dalloc(&c->sc, SC_COUNT));
   LP_TRY(dalloc(&c->fl, FL_COUNT));
@@ -804,6 +810,17 @@ static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
   return LP_OK;
 }
 
+// Q = G G^T (c->Q, full mp x mp) from the hi / lo float planes of G: on the tensor cores
+// (exact digit splitting) or in double-float on the FP32 pipes.
+static lp_status run_gram(lp_ctx* c, const float* Gdf) {
+  if (c->prm.gram_tensor_cores)
+    LP_CU(launch_gram_tc(Gdf, c->ldg, c->m, c->w, c->mp, c->Q, c->gdig, c->gex, c->gpart,
+                         c->num_sms, c->fl, c->st));
+  else
+    LP_CU(launch_gram_df(Gdf, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
+  return LP_OK;
+}
+
 // Probe check of a factor stage: ||(Q + eps diag Q)(M 1) - 1|| / sqrt(m) and the pivot flag.
 static lp_status factor_check(lp_ctx* c, double eps, double* qerr, bool* brk) {
   LP_CU(launch_vec_ops(VOP_ONES, c->res, nullptr, nullptr, c->m, nullptr, c->st));
@@ -857,7 +874,8 @@ static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
   PhaseScope ps(c, LP_PH_FACTOR);
   c->factored = false;
   c->factor_stages = 1;
-  LP_CU(launch_gram(G, c->Gdf, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
+  LP_CU(launch_split_df(G, (size_t)c->ldg * c->w, c->Gdf, c->st));
+  LP_TRY(run_gram(c, c->Gdf));
   double qerr = 0.0;
   bool brk = false;
   LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
@@ -902,7 +920,7 @@ static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
     t.scj = c->ldg;
     LP_CU(launch_df_trmm(t, c->st));
   }
-  LP_CU(launch_gram_df(c->G1df, c->ldg, c->m, c->w, c->mp, c->Q, c->Qsplit, c->qsplit, c->st));
+  LP_TRY(run_gram(c, c->G1df));
   // stage 2
   double eps = 0.0;
   for (;;) {
@@ -1591,6 +1609,9 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   b += (double)round_up(m, 2) * w * 16 + (double)w * 8;                    // G, its split, u
   b += 3.0 * mp * mp * 8;                                                  // Q, M, X
   b += (double)gram_split_cap(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;
+  b += (double)gram_tc_digit_bytes(m, w) + 4.0 * gram_tc_rows(m) +
+       (double)gram_tc_part_bytes(m, mp, w, num_sms);                      // tensor-core Gram
+  b += 3.0 * mp * mp * 8 + (double)round_up(m, 2) * w * 8;               // second factor stage
   b += (SC_COUNT + kMaxRedBlocks * 8) * 8.0 + FL_COUNT * 4 + 64;
   b += 8 * dm + 8 * dn;                                                    // b, c
   if (layout != LP_CSR) {

@@ -147,6 +147,10 @@ struct lp_ctx {
   double* M = nullptr;         // Q^{-1} as double-float pairs (hi, lo: two mp x mp float matrices)
   double* X = nullptr;         // L^{-1} work buffer of the factor, mp x mp
   double* Qsplit = nullptr;    // split-k partials of the Gram product
+  // tensor-core Gram product: digit slices of G, row exponents, double-float partial tiles
+  __nv_bfloat16* gdig = nullptr;
+  int* gex = nullptr;
+  float2* gpart = nullptr;
   int qsplit = 1;
   double shift = 0.0;          // relative diagonal shift used by the last factorization
   // second factor stage (Q numerically singular for the Gram route, e.g. CountSketch late in
@@ -335,6 +339,15 @@ cudaError_t launch_gram(const double* G, float* Gdf, int ldg, int m, int w, int 
                         double* Qsplit, int split, cudaStream_t st);
 cudaError_t launch_gram_df(const float* Gdf, int ldg, int m, int w, int mp, double* Q,
                            double* Qsplit, int split, cudaStream_t st);
+cudaError_t launch_split_df(const double* G, size_t count, float* Gdf, cudaStream_t st);
+// Gram product on the tensor cores (k_gram_tc.cu): exact splitting of the hi / lo planes of G
+// into 8 BF16 digit slices, tcgen05 products accumulated exactly per chunk in TMEM.
+cudaError_t launch_gram_tc(const float* Gdf, int ldg, int m, int w, int mp, double* Q,
+                           __nv_bfloat16* digits, int* ex, float2* part, int num_sms, int* fl,
+                           cudaStream_t st);
+size_t gram_tc_digit_bytes(int m, int w);
+size_t gram_tc_part_bytes(int m, int mp, int w, int num_sms);
+int gram_tc_rows(int m);
 // C = A B in double-float: A lower triangular, row-major planes (Ah, Al) with leading
 // dimension lda; B[k][j] = (Bh, Bl)[k sbk + j sbj] (b_lower: zero for k < j); C[i][j] written
 // at i sci + j scj, and optionally a second copy T at i sti + j stj.  i < M, j < N, k < K.
