@@ -7,7 +7,9 @@ sample of buckets computed one by one from the oracle's hash; the whole IPM thro
 properties that hold at any size (feasibility, duality gap, positivity) recomputed in FP64
 from the GPU's final iterate.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -119,12 +121,32 @@ def _check_solve_invariant(A, lp, solver, m, n):
     assert out["info"].f_norm <= 2.0 * out["info"].f_target
 
 
+class _ChunkedFP64:
+    """A held in its FP32 storage (lp.At, n x m), applied in FP64 one block of columns at a
+    time, so that the host never holds an FP64 copy of a multi-GB matrix."""
+
+    def __init__(self, At, block=50_000):
+        self.At, self.block = At, block
+
+    def matvec(self, x):
+        out = np.zeros(self.At.shape[1])
+        for j in range(0, self.At.shape[0], self.block):
+            out += self.At[j:j + self.block].astype(np.float64).T @ x[j:j + self.block]
+        return out
+
+    def rmatvec(self, y):
+        return np.concatenate([self.At[j:j + self.block].astype(np.float64) @ y
+                               for j in range(0, self.At.shape[0], self.block)])
+
+
 def _check_ipm(A, lp, solver):
     x, y, s, info = solver.solve()
     x, y, s = N(x), N(y), N(s)
     assert info.status == 0
-    rp = np.linalg.norm(A @ x - lp.b) / (1 + np.linalg.norm(lp.b))
-    rd = np.linalg.norm(A.T @ y + s - lp.c) / (1 + np.linalg.norm(lp.c))
+    Ax = A.matvec(x) if isinstance(A, _ChunkedFP64) else A @ x
+    Aty = A.rmatvec(y) if isinstance(A, _ChunkedFP64) else A.T @ y
+    rp = np.linalg.norm(Ax - lp.b) / (1 + np.linalg.norm(lp.b))
+    rd = np.linalg.norm(Aty + s - lp.c) / (1 + np.linalg.norm(lp.c))
     gap = float(x @ s) / (1 + abs(float(lp.c @ x)))
     assert max(rp, rd, gap) <= 1.01e-8
     assert x.min() > 0 and s.min() > 0
@@ -155,12 +177,50 @@ def test_dense_full_products_residuals_sketch(dense_case):
     _check_sketch(A, solver, 1000, 200_000, 5)
 
 
+def _oracle_run(name):
+    """The FP64 oracle's own end-to-end run of a full-size instance, stored by
+    tests/golden/make_oracle_run.py (IPM iterations, objective)."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
+
+
 def test_dense_full_normal_solve_and_ipm(dense_case):
     lp, solver = dense_case
     A = lp.A.astype(np.float64)
     _check_solve_invariant(A, lp, solver, 1000, 200_000)
     info = _check_ipm(A, lp, solver)
-    assert 30 <= info.ipm_iters <= 80
+    # the oracle's own run of this very instance (same W stream, s = 4)
+    ref = _oracle_run("oracle_run_dense_m1000_n200000_f32_s4.json")
+    assert abs(info.ipm_iters - ref["ipm_iters"]) <= 1
+    assert abs(info.obj - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+
+
+def test_dense_fp64_n50000_ipm_matches_oracle():
+    """Config 2 with A in FP64 (n = 50000): the whole IPM on the FP64 path against the oracle's
+    own run of the same instance, plus the FP64 KKT certificate."""
+    import paper_2003_08072_gb300 as pkg
+
+    lp = synth.dense_lp(0, 1000, 50_000)
+    solver = pkg.LPSolver.dense(T(lp.At), T(lp.b), T(lp.c))
+    info = _check_ipm(lp.A, lp, solver)
+    solver.close()
+    ref = _oracle_run("oracle_run_dense_m1000_n50000_f64_s4.json")
+    assert abs(info.ipm_iters - ref["ipm_iters"]) <= 1
+    assert abs(info.obj - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+
+
+def test_scaled_full_bf16_ipm_certificate():
+    """Config 4 (m = 2000, n = 500000, column scales 10^U(-3,3)) with A streamed in BF16 plus
+    FP64 refinement: the whole solve to the stopping rule, certified in FP64 on the host."""
+    import paper_2003_08072_gb300 as pkg
+
+    lp = synth.dense_lp(0, 2000, 500_000, dtype=np.float32, col_scale=(-3, 3))
+    prm = pkg.lp_params_default()
+    prm.stream_dtype = pkg.LP_BF16
+    solver = pkg.LPSolver.dense(T(lp.At), T(lp.b), T(lp.c), params=prm)
+    info = _check_ipm(_ChunkedFP64(lp.At), lp, solver)
+    solver.close()
+    assert 20 <= info.ipm_iters <= 80
 
 
 def test_sparse_full_products_residuals_sketch(sparse_case):
@@ -175,3 +235,10 @@ def test_sparse_full_normal_solve(sparse_case):
     lp, solver = sparse_case
     S = lp.to_scipy()
     _check_solve_invariant(S, lp, solver, lp.m, lp.n)
+
+
+def test_sparse_full_ipm_certificate(sparse_case):
+    """Config 3 (m = 5000, n = 2,000,000, CSR): the whole IPM, certified in FP64 on the host."""
+    lp, solver = sparse_case
+    info = _check_ipm(lp.to_scipy(), lp, solver)
+    assert 30 <= info.ipm_iters <= 100
