@@ -86,6 +86,8 @@ def parse_args():
     ap.add_argument("--no-gram-tc", action="store_true",
                     help="Gram product of the factor in double-float on the FP32 pipes instead "
                          "of the tensor cores")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed launch-shape rule for the CG product instead of the autotuner")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven CG loop instead of one CUDA graph launch per CG solve")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -369,6 +371,7 @@ def run_ours(args, rank, world, local):
     prm.cg_batch = args.cg_batch
     prm.use_graphs = 0 if args.no_graphs else 1
     prm.gram_tensor_cores = 0 if args.no_gram_tc else 1
+    prm.autotune = 0 if args.no_autotune else 1
     sparse = args.workload == "sparse"
     sd = (args.dtype if not sparse else "f32") if args.stream == "same" else args.stream
     prm.stream_dtype = pkg.DTYPE_CODES[sd] if not sparse else pkg.LP_F64
@@ -510,6 +513,7 @@ def run_ours(args, rank, world, local):
             "timing": "CUDA events on the library's stream around every CG product of one "
                       "profiled LP solve run after the timed steps (the timed steps run without "
                       "events)",
+            "autotune": prof.as_dict()["tune"],
         },
         "e2e": {"value": (world * k_e2e / e2e_t) if k_e2e else None, "unit": "LP/s",
                 "h2d_bytes_per_step": h2d,

@@ -96,9 +96,13 @@ typedef struct {
                             is enqueued by the host and the stop flag read every cg_batch
                             iterations.  Profiling (lp_profile_enable) runs the host-driven loop (1) */
   int32_t gram_tensor_cores; /* 1: the Gram product Q = (A D W)(A D W)^T of the factor runs on the tensor
-                            cores (tcgen05), made exact by splitting each row of the sketch into eight
-                            BF16 digit slices of 6 bits (accurate to ~2^-48 of |G_i| |G_j| w, as the
-                            double-float product); 0: double-float product on the FP32 pipes (1) */
+                            cores (tcgen05), made exact by splitting each row of the sketch into nine
+                            BF16 digit slices of 6 bits (each entry accurate to ~2^-52 sqrt(w)
+                            |G_i| |G_j|, finer than the double-float product); 0: double-float product
+                            on the FP32 pipes (1) */
+  int32_t autotune;      /* 1: lp_create times the CG product's launch shapes (group width, pipeline
+                            stages, CTAs per SM) on the matrix itself (A of 64 MB and more; a few ms,
+                            kept per shape for the process) and keeps the fastest; 0: fixed rule (1) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */
@@ -361,6 +365,11 @@ typedef struct {
   int64_t matvec_count;             /* number of those launches */
   double matvec_bytes;              /* algorithmic bytes of one CG product (read of A, D^2, v) */
   int64_t launches;                 /* kernel launches issued by the library since load (all contexts) */
+  int32_t tune_tc, tune_stages, tune_ctas; /* autotuned CG product shape for the copy streamed now
+                                              (columns per copy, stages, CTAs per SM); 0: the fixed
+                                              rule (not tuned, or no candidate beat it) */
+  double tune_us, tune_rule_us;     /* measured time per product of the shape in use and of the
+                                       fixed rule (0 when the copy was not tuned) */
 } lp_profile;
 
 /*

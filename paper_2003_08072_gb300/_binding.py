@@ -42,6 +42,7 @@ class lp_params(ctypes.Structure):
         ("sketch_kind", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
         ("gram_tensor_cores", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -92,6 +93,11 @@ class lp_profile(ctypes.Structure):
         ("matvec_count", ctypes.c_int64),
         ("matvec_bytes", ctypes.c_double),
         ("launches", ctypes.c_int64),
+        ("tune_tc", ctypes.c_int32),
+        ("tune_stages", ctypes.c_int32),
+        ("tune_ctas", ctypes.c_int32),
+        ("tune_us", ctypes.c_double),
+        ("tune_rule_us", ctypes.c_double),
     ]
 
     PHASES = ("residuals", "sketch", "factor", "pcg", "rtilde", "correction", "update", "other")
@@ -102,6 +108,9 @@ class lp_profile(ctypes.Structure):
             "phase_calls": {k: int(self.phase_calls[i]) for i, k in enumerate(self.PHASES)},
             "matvec_ms": self.matvec_ms, "matvec_count": int(self.matvec_count),
             "matvec_bytes": self.matvec_bytes, "launches": int(self.launches),
+            "tune": {"tc": self.tune_tc, "stages": self.tune_stages,
+                     "ctas_per_sm": self.tune_ctas, "us": self.tune_us,
+                     "rule_us": self.tune_rule_us},
         }
 
 

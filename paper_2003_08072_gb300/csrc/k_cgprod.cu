@@ -347,20 +347,30 @@ constexpr bool keep_default() {
   return sizeof(TA) == 2;
 }
 
+constexpr size_t kSmemTuneLimit = 220 * 1024;   // what a tuned shape may use per SM
+
 template <typename TA, int SPW, int TC>
 int launch_cgprod_t(ColArgs a, int nwarps, int num_sms, int max_grid, cudaStream_t st) {
   const size_t col_bytes = (size_t)a.lda * sizeof(TA);
   const size_t stage = (size_t)TC * col_bytes;
-  // enough warps per SM to hide shared-memory latency: up to 4 CTAs of few warps
-  int ctas = std::max(1, std::min(4, 16 / nwarps));
-  int S = 0;
-  for (; ctas >= 1; --ctas) {
-    S = (int)std::min<size_t>(6, (kSmemBudget / ctas) / (stage + 8));
-    if (S >= 3) break;
-  }
-  if (ctas < 1) {
-    ctas = 1;
-    S = (int)std::min<size_t>(6, kSmemBudget / (stage + 8));
+  int ctas = 0, S = 0;
+  if (a.cfg_ctas > 0 && a.cfg_stages >= 2 &&
+      (size_t)a.cfg_ctas * a.cfg_stages * (stage + 8) <= kSmemTuneLimit &&
+      a.cfg_ctas * nwarps * 32 <= 2048) {
+    // the shape the autotuner measured fastest for this matrix
+    ctas = a.cfg_ctas;
+    S = a.cfg_stages;
+  } else {
+    // rule: enough warps per SM to hide shared-memory latency, up to 4 CTAs of few warps
+    ctas = std::max(1, std::min(4, 16 / nwarps));
+    for (; ctas >= 1; --ctas) {
+      S = (int)std::min<size_t>(6, (kSmemBudget / ctas) / (stage + 8));
+      if (S >= 3) break;
+    }
+    if (ctas < 1) {
+      ctas = 1;
+      S = (int)std::min<size_t>(6, kSmemBudget / (stage + 8));
+    }
   }
   if (S < 2) return -1;
   const size_t smem = (size_t)S * stage + (size_t)S * 8;
@@ -386,8 +396,10 @@ int launch_cgprod_dt(ColArgs a, int num_sms, int max_grid, cudaStream_t st) {
   while ((nslices + spw - 1) / spw > 16) spw *= 2;
   if (spw > 4) return -1;
   const int nwarps = (nslices + spw - 1) / spw;
-  // groups of 8 columns while a stage stays within 64 KB, else of 2
-  const bool wide_cols = (size_t)8 * a.lda * sizeof(TA) > 64 * 1024;
+  // groups of 8 columns while a stage stays within 64 KB, else of 2 (or the tuned width)
+  bool wide_cols = (size_t)8 * a.lda * sizeof(TA) > 64 * 1024;
+  if (a.cfg_tc == 2) wide_cols = true;
+  if (a.cfg_tc == 8 && (size_t)8 * a.lda * sizeof(TA) * 2 <= kSmemTuneLimit) wide_cols = false;
   switch (spw) {
     case 1:
       return wide_cols ? launch_cgprod_t<TA, 1, 2>(a, nwarps, num_sms, max_grid, st)
@@ -402,6 +414,74 @@ int launch_cgprod_dt(ColArgs a, int num_sms, int max_grid, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Autotuner of the launch shape: group width TC (columns per bulk copy), pipeline stages S
+// and CTAs per SM, timed with CUDA events on the matrix itself (a few launches per candidate,
+// writing per-CTA partial sums only).  The fastest candidate is returned together with the
+// time of the fixed rule, so the choice can be reported.
+int tune_cgprod(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t st,
+                CgTune* out) {
+  const size_t es = ta == LP_F32 ? 4 : 2;
+  if (ta != LP_F32 && ta != LP_BF16 && ta != LP_F16) return -1;
+  const int vec = (int)(16 / es);
+  const int nslices = (a.m + 32 * vec - 1) / (32 * vec);
+  int spw = 1;
+  while ((nslices + spw - 1) / spw > 16) spw *= 2;
+  if (spw > 4) return -1;
+  const int nwarps = (nslices + spw - 1) / spw;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return -1;
+  }
+  auto time_it = [&](ColArgs b) -> float {
+    if (launch_cgprod(ta, b, num_sms, max_grid, st) < 0) return -1.f;   // warm-up
+    cudaEventRecord(e0, st);
+    constexpr int kReps = 3;
+    for (int r = 0; r < kReps; ++r)
+      if (launch_cgprod(ta, b, num_sms, max_grid, st) < 0) return -1.f;
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      return -1.f;
+    }
+    return 1000.f * ms / kReps;
+  };
+  a.qacc = nullptr;   // partial sums only: nothing of the CG state is touched
+  a.skip_if_done = 0;
+  a.dz = nullptr;
+  a.cfg_tc = a.cfg_stages = a.cfg_ctas = 0;
+  CgTune best{};
+  best.rule_us = time_it(a);
+  best.us = best.rule_us;
+  for (int tc : {8, 2}) {
+    const size_t stage = (size_t)tc * a.lda * es;
+    if (tc == 8 && 2 * stage > kSmemTuneLimit) continue;
+    for (int ctas = 1; ctas <= 4; ++ctas) {
+      if (ctas * nwarps * 32 > 2048) continue;
+      for (int S = 2; S <= 6; ++S) {
+        if ((size_t)ctas * S * (stage + 8) > kSmemTuneLimit) continue;
+        ColArgs b = a;
+        b.cfg_tc = tc;
+        b.cfg_stages = S;
+        b.cfg_ctas = ctas;
+        const float us = time_it(b);
+        if (us > 0.f && (best.us <= 0.f || us < best.us)) {
+          best.us = us;
+          best.tc = tc;
+          best.stages = S;
+          best.ctas = ctas;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *out = best;   // ctas == 0: no candidate beat the fixed rule, which stays in use
+  return best.rule_us > 0.f ? 0 : -1;
+}
 
 // Returns the number of CTAs (partial rows) or -1 when the shape is not covered (the caller
 // then uses the register-tiled pass).  Needs a.d2f (the FP32 weight).

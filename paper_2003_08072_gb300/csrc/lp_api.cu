@@ -87,6 +87,7 @@ lp_status lp_params_default(lp_params* p) {
   p->sketch_kind = LP_SKETCH_SPARSE;
   p->use_graphs = 1;
   p->gram_tensor_cores = 1;
+  p->autotune = 1;
   return LP_OK;
 }
 
@@ -372,6 +373,47 @@ static lp_status check_finite_dev(lp_ctx* c, const void* p, lp_dtype dt, int64_t
   return LP_OK;
 }
 
+// Autotunes the staged CG product's launch shape for the copy of A of dtype ta (the streamed
+// copy, or the master copy a solve may switch to).  Matrices below 64 MB keep the fixed rule
+// (the candidates would cost more than they save); results are kept per shape for the process.
+static void autotune_cgprod(lp_ctx* c, lp_dtype ta, const void* A, int lda) {
+  if (!c->prm.autotune || c->sparse || (ta != LP_F32 && ta != LP_BF16 && ta != LP_F16)) return;
+  if ((double)c->m * (double)c->n * (double)dtype_size(ta) < 64e6) return;
+  static std::mutex mu;
+  static std::vector<std::pair<std::vector<int64_t>, CgTune>> cache;
+  const std::vector<int64_t> key{(int64_t)ta, c->m, lda, c->n, c->num_sms, c->dev};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& kv : cache)
+      if (kv.first == key) {
+        c->tune[(int)ta & 3] = kv.second;
+        return;
+      }
+  }
+  if (cudaMemsetAsync(c->d2f, 0, (size_t)c->n * sizeof(float), c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->z, 0, (size_t)c->m * sizeof(double), c->st) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  ColArgs a{};
+  a.A = A;
+  a.lda = lda;
+  a.m = c->m;
+  a.n = c->n;
+  a.v = c->z;
+  a.d2f = c->d2f;
+  a.part = c->part;
+  a.fl = c->fl;
+  a.flw = c->fl;
+  CgTune t{};
+  if (tune_cgprod(ta, a, c->num_sms, coltile_max_grid(c->num_sms), c->st, &t) == 0) {
+    c->tune[(int)ta & 3] = t;
+    std::lock_guard<std::mutex> lk(mu);
+    cache.push_back({key, t});
+  }
+  cudaGetLastError();
+}
+
 extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout layout,
                                lp_dtype a_dtype, const void* A_vals, const int64_t* indptr,
                                const int32_t* indices, int64_t nnz, const double* b,
@@ -528,6 +570,10 @@ extern "C" lp_status lp_create(lp_ctx** out, int32_t m, int64_t n, lp_layout lay
   c->As_req = c->As;
   c->lda_s_req = c->lda_s;
   c->svals_req = c->svals;
+  if (!c->sparse) {
+    autotune_cgprod(c, c->s_dtype, c->As, c->lda_s);
+    if (c->a_dtype != c->s_dtype) autotune_cgprod(c, c->a_dtype, c->A, c->lda);
+  }
   // norms of b and c for the stopping rule
   LP_CU(launch_norm2(c->b, m, c->sc, SC_RES2, c->bpart, c->bcnt, c->st));
   if ((st = sync_scalars(c)) != LP_OK) return bail(st);
@@ -601,6 +647,10 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     if (!acc64 && a.d2f && c->use_staged) {
       a.stall_group_p1 = c->stall_group_p1;   // fault injection: next staged product only
       a.wait_ns = c->stall_wait_ns;
+      const CgTune& tn = c->tune[(int)ta & 3];
+      a.cfg_tc = tn.tc;
+      a.cfg_stages = tn.stages;
+      a.cfg_ctas = tn.ctas;
       nblk = launch_cgprod(ta, a, c->num_sms, coltile_max_grid(c->num_sms), c->st);
       if (nblk >= 0) {
         c->stall_group_p1 = 0;
@@ -1648,6 +1698,12 @@ extern "C" lp_status lp_profile_read(lp_ctx* c, lp_profile* out, int32_t reset) 
   c->prof.matvec_bytes = c->prof.matvec_count > 0 ? c->mv_bytes_sum / c->prof.matvec_count
                                                   : matvec_bytes(c);
   c->prof.launches = g_launches.load();
+  const CgTune& tn = c->tune[(int)c->s_dtype & 3];
+  c->prof.tune_tc = tn.tc;
+  c->prof.tune_stages = tn.stages;
+  c->prof.tune_ctas = tn.ctas;
+  c->prof.tune_us = tn.us;
+  c->prof.tune_rule_us = tn.rule_us;
   *out = c->prof;
   if (reset) {
     c->prof = lp_profile{};

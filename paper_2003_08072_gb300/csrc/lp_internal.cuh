@@ -62,6 +62,13 @@ constexpr int kNB = 32;          // block size of the blocked Cholesky inverse
 constexpr int kQCopies = 8;      // copies of the atomically accumulated CG product
 constexpr int kMaxRedBlocks = 1024;
 
+// Launch shape of the staged CG product picked by the autotuner, with its measured time and
+// the time of the fixed rule on the same matrix.
+struct CgTune {
+  int tc = 0, stages = 0, ctas = 0;
+  float us = 0.f, rule_us = 0.f;
+};
+
 }  // namespace lpk
 
 struct lp_ctx {
@@ -96,6 +103,7 @@ struct lp_ctx {
   int precise_iter = -1;       // IPM iteration of that escalation (-1: none)
   lp_ipm_state ipm_state{0, -1, 0.0, 0.0};  // Algorithm 2's state at the end of the last run
   bool use_staged = true;      // CG products through the shared-memory staged pass
+  lpk::CgTune tune[4];         // autotuned launch shape of the staged product per stream dtype
   // fault injection for the next staged CG product only (lp_test_stall_copy)
   int64_t stall_group_p1 = 0;
   uint64_t stall_wait_ns = 0;
@@ -254,7 +262,10 @@ struct ColArgs {
   // zero-initialised ColArgs injects nothing)
   uint64_t wait_ns;
   int64_t stall_group_p1;
+  // staged CG product only: a launch shape chosen by the autotuner (0: the fixed rule)
+  int cfg_tc, cfg_stages, cfg_ctas;
 };
+
 
 // Dense column-tile pass.  acc_f64 selects FP64 accumulation (else FP32).
 // Returns the number of CTAs used (partials rows), or -1 on an unsupported shape.
@@ -262,6 +273,7 @@ int launch_coltile(lp_dtype ta, bool acc_f64, int mode, ColArgs a, int num_sms, 
 // CG product (MODE_NORMAL, FP32 accumulation, FP32 weight a.d2f) with A staged through shared
 // memory by bulk copies (k_cgprod.cu); -1 when the shape or dtype is not covered.
 int launch_cgprod(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t st);
+int tune_cgprod(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t st, CgTune* out);
 
 // Sparse (CSC) passes
 struct CscArgs {
