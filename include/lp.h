@@ -103,6 +103,10 @@ typedef struct {
   int32_t autotune;      /* 1: lp_create times the CG product's launch shapes (group width, pipeline
                             stages, CTAs per SM) on the matrix itself (A of 64 MB and more; a few ms,
                             kept per shape for the process) and keeps the fastest; 0: fixed rule (1) */
+  int32_t shared_cg;     /* serving loop only (read by lp_server_create): 1 = the live instances' CG
+                            iterations share launches through the server's batch engine; 0 = each
+                            instance runs its own CG loop (one CUDA graph launch per CG solve, the
+                            instances overlapping on their own streams) (0) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */
@@ -412,6 +416,12 @@ uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, lp_dtype a_d
  * as its lp_footprint_bytes fits into the part of mem_budget_bytes not held by live requests,
  * solves it with lp_create + lp_ipm_solve (Algorithm 2, parameters prm) and releases the memory.
  * Live instances run concurrently on the GPU.  Admission is first come, first served.
+ * With prm->shared_cg and max_live > 1 the CG iterations of the live instances share
+ * launches: an instance whose solve reaches a CG loop over a dense A streamed below FP64 hands
+ * the loop to the server's batch engine, which advances every such loop by one iteration per
+ * round with one batched product launch and one batched preconditioner launch over a
+ * per-instance work table (each instance keeps its own scalars and stop rule; results are
+ * those of the instance solved alone up to the order of floating-point sums).
  * All buffers passed to the server are HOST memory; submit copies them, so the caller may
  * reuse its buffers as soon as lp_server_submit returns.  One server per device; the device is
  * the calling thread's current one at creation.  A server may be used from several threads.
@@ -422,6 +432,9 @@ typedef struct {
   int64_t submitted, completed, failed;   /* counts since creation (failed: status != LP_OK) */
   int64_t queued, live, peak_live;        /* waiting, being solved, most solved at once */
   uint64_t mem_in_use, mem_peak, mem_budget;  /* admitted footprints (bytes) */
+  int64_t batched_rounds;    /* rounds of shared CG launches run (one CG iteration of every
+                                live instance's CG solve per round) */
+  int64_t batched_cg_solves; /* CG solves that ran in shared launches */
 } lp_server_stats_t;
 
 /* Errors: LP_ERR_ARG (max_live outside 1..256, zero budget), LP_ERR_CUDA (no device). */

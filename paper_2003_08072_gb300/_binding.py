@@ -43,6 +43,7 @@ class lp_params(ctypes.Structure):
         ("use_graphs", ctypes.c_int32),
         ("gram_tensor_cores", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("shared_cg", ctypes.c_int32),
     ]
 
 
@@ -120,6 +121,7 @@ class lp_server_stats_t(ctypes.Structure):
         ("queued", ctypes.c_int64), ("live", ctypes.c_int64), ("peak_live", ctypes.c_int64),
         ("mem_in_use", ctypes.c_uint64), ("mem_peak", ctypes.c_uint64),
         ("mem_budget", ctypes.c_uint64),
+        ("batched_rounds", ctypes.c_int64), ("batched_cg_solves", ctypes.c_int64),
     ]
 
     def as_dict(self):

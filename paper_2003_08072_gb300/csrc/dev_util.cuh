@@ -120,16 +120,19 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 // Grid-wide sum with the "last block finishes" pattern (no spin wait): each block
 // writes its NV partials, the last block to arrive sums all partials in block order
 // (deterministic) and returns true in all of its threads with v holding the totals.
+// The same over a virtual grid of nblk blocks (bid = this block's index in it): a batched
+// launch runs several such grids, one per job of its work table.
 template <int NV>
-__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* bpart, unsigned* counter) {
+__device__ __forceinline__ bool grid_sum_last_b(double (&v)[NV], double* bpart, unsigned* counter,
+                                                unsigned bid, unsigned nblk) {
   __shared__ bool s_last;
   block_sum<NV>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) bpart[blockIdx.x * NV + k] = v[k];
+    for (int k = 0; k < NV; ++k) bpart[bid * NV + k] = v[k];
     __threadfence();
     unsigned ticket = atomicAdd(counter, 1u);
-    s_last = (ticket == gridDim.x - 1);
+    s_last = (ticket == nblk - 1);
   }
   __syncthreads();
   if (!s_last) return false;
@@ -138,7 +141,7 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* bpart, un
   double tot[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) tot[k] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+  for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < NV; ++k) tot[k] += __ldcg(&bpart[b * NV + k]);
   block_sum<NV>(tot);
@@ -152,6 +155,11 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* bpart, un
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = s_tot[k];
   return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* bpart, unsigned* counter) {
+  return grid_sum_last_b<NV>(v, bpart, counter, blockIdx.x, gridDim.x);
 }
 
 // Grid-wide minimum, same pattern.

@@ -101,9 +101,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 
 }  // namespace
 
-// Shared memory: S stages of TC * lda elements, then S mbarriers.
+// Shared memory: S stages of TC * lda elements, then S mbarriers.  The body runs as block bid
+// of a grid of nblk blocks: the whole launch (k_cgprod) or one job's share of a batched launch
+// (k_cgprod_batch).
 template <typename TA, int SPW, int TC, bool KEEP>
-__global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroups) {
+__device__ __forceinline__ void cgprod_body(const ColArgs& a, int S, int64_t ngroups, int bid,
+                                            int nblk) {
   constexpr int VEC = VecN<TA>::N;
   constexpr bool COMP = sizeof(TA) == 4;   // compensated row sums for FP32 copies
   extern __shared__ __align__(128) unsigned char smem[];
@@ -116,16 +119,15 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * stage_elems * sizeof(TA));
   const TA* A = reinterpret_cast<const TA*>(a.A);
 
-  // groups of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
-  const int my_groups =
-      blockIdx.x < ngroups ? (int)((ngroups - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
-  const int64_t col_step = (int64_t)gridDim.x * TC;
+  // groups of this CTA: bid, bid + nblk, ...
+  const int my_groups = bid < ngroups ? (int)((ngroups - 1 - bid) / nblk) + 1 : 0;
+  const int64_t col_step = (int64_t)nblk * TC;
   const uint64_t wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
   auto issue = [&](int i, int stage) {   // thread 0: copy local group i into a stage
     // fault-injection hook: CTA 0 never issues the copy of its group stall_group, so the
     // wait for it runs out (its stage keeps stale data; nothing is written out of bounds)
-    if (blockIdx.x == 0 && (int64_t)i + 1 == a.stall_group_p1) return;
-    const int64_t col0 = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * TC;
+    if (bid == 0 && (int64_t)i + 1 == a.stall_group_p1) return;
+    const int64_t col0 = ((int64_t)bid + (int64_t)i * nblk) * TC;
     const int ncols = (int)std::min<int64_t>(TC, a.n - col0);
     const unsigned bytes = (unsigned)((size_t)ncols * a.lda * sizeof(TA));
     uint64_t* bar = &bars[stage];
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
       if (rok[sl] && row < a.m) {
         if (a.dz) {   // fused CG direction update d = z + beta d_old
           x = fma(a.sc[SC_BETA], a.dold[row], a.dz[row]);
-          if (blockIdx.x == 0) a.dnew[row] = x;
+          if (bid == 0) a.dnew[row] = x;
         } else {
           x = a.v[row];
         }
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
   // stage of group i is i % S and its phase parity (i / S) & 1, both kept as running counters
   int stage = 0, prev_stage = S - 1;
   unsigned parity = 0;
-  int64_t col0 = (int64_t)blockIdx.x * TC;
+  int64_t col0 = (int64_t)bid * TC;
   for (int i = 0; i < my_groups; ++i, col0 += col_step) {
     const TA* st = stages + (size_t)stage * stage_elems;
     // after one wait has given up, the rest are skipped (and no further copies issued)
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
 
   if (a.qacc) {
     // kQCopies copies of q spread the atomic traffic over more L2 lines
-    double* qc = a.qacc + (size_t)(blockIdx.x % kQCopies) * a.m;
+    double* qc = a.qacc + (size_t)(bid % kQCopies) * a.m;
 #pragma unroll
     for (int sl = 0; sl < SPW; ++sl)
 #pragma unroll
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
     __shared__ bool s_last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(a.cnt, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(a.cnt, 1u) == (unsigned)nblk - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -330,8 +332,33 @@ __global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroup
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int row = rowb[sl] + e;
-      if (rok[sl] && row < a.m) part[(size_t)blockIdx.x * a.m + row] = (float)row_sum(sl, e);
+      if (rok[sl] && row < a.m) part[(size_t)bid * a.m + row] = (float)row_sum(sl, e);
     }
+}
+
+template <typename TA, int SPW, int TC, bool KEEP>
+__global__ void __launch_bounds__(512) k_cgprod(ColArgs a, int S, int64_t ngroups) {
+  cgprod_body<TA, SPW, TC, KEEP>(a, S, ngroups, blockIdx.x, gridDim.x);
+}
+
+// Batched CG product: every CTA finds its job in the work table (sorted by cta0) and runs that
+// job's product as block (blockIdx.x - cta0) of a grid of ncta blocks.
+template <typename TA, int SPW, int TC, bool KEEP>
+__global__ void __launch_bounds__(512) k_cgprod_batch(const CgProdJob* __restrict__ jobs,
+                                                      int njobs) {
+  __shared__ int s_job;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {   // last job with cta0 <= blockIdx.x
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].cta0 <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    s_job = lo;
+  }
+  __syncthreads();
+  const CgProdJob& jb = jobs[s_job];
+  cgprod_body<TA, SPW, TC, KEEP>(jb.a, jb.S, jb.ngroups, (int)blockIdx.x - jb.cta0, jb.ncta);
 }
 
 namespace {
@@ -481,6 +508,52 @@ int tune_cgprod(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t 
   cudaEventDestroy(e1);
   *out = best;   // ctas == 0: no candidate beat the fixed rule, which stays in use
   return best.rule_us > 0.f ? 0 : -1;
+}
+
+// ---- batched CG products (the serving loop's shared launches) --------------------------
+
+bool cgprod_job_shape(lp_dtype ta, int m, int lda, int64_t n, int* tc, int* nwarps, int* S,
+                      int64_t* ngroups, size_t* smem) {
+  if (ta != LP_F32 && ta != LP_BF16 && ta != LP_F16) return false;
+  const size_t es = ta == LP_F32 ? 4 : 2;
+  const int vec = (int)(16 / es);
+  const int nslices = (m + 32 * vec - 1) / (32 * vec);
+  if (nslices > 16) return false;   // one row slice per warp (SPW = 1) only
+  *nwarps = nslices;
+  *tc = ((size_t)8 * lda * es > 64 * 1024) ? 2 : 8;
+  const size_t stage = (size_t)(*tc) * lda * es;
+  *S = 3;
+  *ngroups = (n + *tc - 1) / *tc;
+  *smem = (size_t)(*S) * stage + (size_t)(*S) * 8;
+  return true;
+}
+
+template <typename TA, int TC>
+cudaError_t launch_cgprod_batch_t(const CgProdJob* jobs, int njobs, int total_ctas, int nwarps,
+                                  size_t smem, cudaStream_t st) {
+  auto kern = k_cgprod_batch<TA, 1, TC, keep_default<TA>()>;
+  cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
+  { note_launch(); kern<<<total_ctas, nwarps * 32, smem, st>>>(jobs, njobs); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cgprod_batch(lp_dtype ta, int tc, const CgProdJob* jobs, int njobs,
+                                int total_ctas, int nwarps, size_t smem, cudaStream_t st) {
+  switch (ta) {
+    case LP_F32:
+      return tc == 2 ? launch_cgprod_batch_t<float, 2>(jobs, njobs, total_ctas, nwarps, smem, st)
+                     : launch_cgprod_batch_t<float, 8>(jobs, njobs, total_ctas, nwarps, smem, st);
+    case LP_BF16:
+      return tc == 2
+                 ? launch_cgprod_batch_t<__nv_bfloat16, 2>(jobs, njobs, total_ctas, nwarps, smem, st)
+                 : launch_cgprod_batch_t<__nv_bfloat16, 8>(jobs, njobs, total_ctas, nwarps, smem, st);
+    case LP_F16:
+      return tc == 2 ? launch_cgprod_batch_t<__half, 2>(jobs, njobs, total_ctas, nwarps, smem, st)
+                     : launch_cgprod_batch_t<__half, 8>(jobs, njobs, total_ctas, nwarps, smem, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 // Returns the number of CTAs (partial rows) or -1 when the shape is not covered (the caller

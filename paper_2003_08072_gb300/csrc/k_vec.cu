@@ -147,35 +147,14 @@ cudaError_t launch_norm2(const double* v, int64_t n, double* sc, int slot, doubl
 // Preconditioner apply z = M r (M = Q^{-1}, full symmetric, row-major, leading dim mp),
 // warp per row, r staged in shared memory; fused r^T z with CG bookkeeping.
 // ------------------------------------------------------------------------------------
-struct SymvArgs {
-  const double* M;
-  int mp, m;
-  const double* r;
-  double* z;
-  double* sc;
-  int* fl;
-  double* bpart;
-  unsigned* bcnt;
-  int mode;
-  double rel2;     // CG relative tolerance squared (CG_INIT)
-  // fused residual update (CG_STEP): r = rold - alpha q; CTA 0 stores r and dy += alpha d
-  const double* rold;
-  const double* q;
-  const double* d;
-  double* dy;
-  const double* qf;    // the product's atomic q copies (q itself holds their sum)
-  double* qzero;       // zeroed by CTA 0 for the next CG product
-  // factored preconditioner M = X^T X (X = L^{-1}, lower triangular): the first of its two
-  // products, t = X r, forms rho = r^T M r as ||t||^2 (sq); the second, z = X^T t, does no
-  // bookkeeping and is skipped once the solve has finished (skip_done)
-  int sq;
-  int skip_done;
-};
+
 
 // DF: M holds double-float pairs (Mh = (float*)M, Ml = Mh + mp^2) and the row sums run on the
 // FP32 pipes; otherwise M is FP64.
+// The body runs as block bid of a grid of nblk blocks (rows 8 bid .. 8 bid + 7): the whole
+// launch (k_symv) or one job's share of a batched launch (k_symv_batch).
 template <bool DF>
-__global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
+__device__ __forceinline__ void symv_body(const SymvArgs& a, int bid, int nblk) {
   if ((a.mode == SYMV_CG_STEP || a.skip_done) && a.fl[FL_DONE]) return;
   extern __shared__ double rs[];
   const int m4 = (a.m + 3) & ~3;                      // rows of M are padded (mp >= m4)
@@ -189,7 +168,7 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
         // with atomic copies the product's last CTA has already summed them into q
         const double qi = a.q[i];
         v = fma(-al, qi, a.rold[i]);
-        if (blockIdx.x == 0) {
+        if (bid == 0) {
           const_cast<double*>(a.r)[i] = v;
           a.dy[i] = fma(al, a.d[i], a.dy[i]);
           if (a.qzero)
@@ -205,7 +184,7 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = blockIdx.x * 8 + warp;
+  const int row = bid * 8 + warp;
   double dotc = 0.0;
   if (row < a.m) {
     double acc;
@@ -245,7 +224,7 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
   }
   if (a.mode == SYMV_PLAIN) return;
   double v[1] = {dotc};
-  if (!grid_sum_last<1>(v, a.bpart, a.bcnt) || threadIdx.x != 0) return;
+  if (!grid_sum_last_b<1>(v, a.bpart, a.bcnt, bid, nblk) || threadIdx.x != 0) return;
   const double rho = v[0];
   if (a.mode == SYMV_F2) {
     a.sc[SC_F2] = rho;
@@ -277,6 +256,27 @@ __global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
       a.fl[FL_DONE] = 1;
     }
   }
+}
+
+template <bool DF>
+__global__ void __launch_bounds__(256) k_symv(SymvArgs a) {
+  symv_body<DF>(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_symv_batch(const SymvJob* __restrict__ jobs, int njobs) {
+  __shared__ int s_job;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {   // last job with cta0 <= blockIdx.x
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].cta0 <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    s_job = lo;
+  }
+  __syncthreads();
+  const SymvJob& jb = jobs[s_job];
+  symv_body<true>(jb.a, (int)blockIdx.x - jb.cta0, jb.ncta);
 }
 
 // Preconditioner apply with M = Q^{-1} stored as DF pairs.
@@ -350,6 +350,14 @@ __global__ void k_cg_cond(cudaGraphConditionalHandle h, int* fl, int max_trips) 
 
 cudaError_t launch_cg_cond(cudaGraphConditionalHandle h, int* fl, int max_trips, cudaStream_t st) {
   { note_launch(); k_cg_cond<<<1, 1, 0, st>>>(h, fl, max_trips); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symv_batch(const SymvJob* jobs, int njobs, int total_ctas, size_t smem,
+                              cudaStream_t st) {
+  cudaError_t e = ensure_dyn_smem((const void*)k_symv_batch, smem);
+  if (e != cudaSuccess) return e;
+  { note_launch(); k_symv_batch<<<total_ctas, 256, smem, st>>>(jobs, njobs); }
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "lp_batch.cuh"
 #include "lp_internal.cuh"
 
 using namespace lpk;
@@ -88,6 +89,7 @@ lp_status lp_params_default(lp_params* p) {
   p->use_graphs = 1;
   p->gram_tensor_cores = 1;
   p->autotune = 1;
+  p->shared_cg = 0;
   return LP_OK;
 }
 
@@ -215,6 +217,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (auto& g : c->cg_graphs) cg_graph_free(g);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  if (c->batch_ready) cudaEventDestroy(c->batch_ready);
   delete c;
 }
 
@@ -1198,6 +1201,64 @@ static lp_status cg_graph_launch(lp_ctx* c, const CgLoop& L, int max_iter, bool*
   return LP_OK;
 }
 
+// Runs the CG loop of L (op 0, staged FP32-accumulated product) in the serving loop's batch
+// engine: the launch descriptors of both iteration parities, exactly those cg_iteration would
+// launch, go into a job.  *taken is false when the matrix or the engine cannot take it.
+static lp_status cg_batch_solve(lp_ctx* c, const CgLoop& L, bool* taken) {
+  *taken = false;
+  int tc = 8, nwarps = 1, S = 3;
+  int64_t ngroups = 0;
+  size_t smem = 0;
+  if (!cgprod_job_shape(c->s_dtype, c->m, c->lda_s, c->n, &tc, &nwarps, &S, &ngroups, &smem))
+    return LP_OK;
+  if (!c->batch_ready) LP_CU(cudaEventCreateWithFlags(&c->batch_ready, cudaEventDisableTiming));
+  CgBatchJob j;
+  j.c = c;
+  j.ta = c->s_dtype;
+  j.tc = tc;
+  j.nwarps = nwarps;
+  j.prod_smem = smem;
+  j.prod_ctas = cg_batch_prod_ctas(c, dtype_size(c->s_dtype), c->num_sms, ngroups);
+  j.symv_ctas = (c->m + 7) / 8;
+  j.symv_smem = (size_t)((c->m + 3) & ~3) * 2 * sizeof(double);
+  j.factored = c->factored;
+  j.ready = c->batch_ready;
+  for (int p = 0; p < 2; ++p) {
+    ColArgs a{};
+    a.A = c->As;
+    a.lda = c->lda_s;
+    a.m = c->m;
+    a.n = c->n;
+    a.d2 = c->d2;
+    a.d2f = c->d2f;
+    a.part = c->part;
+    a.fl = c->fl;
+    a.sc = c->sc;
+    a.skip_if_done = 1;
+    a.dz = c->z;
+    a.dold = L.d[(p + 1) & 1];
+    a.dnew = L.d[p];
+    a.flw = c->fl;
+    a.qacc = L.q[p];
+    a.qsum = c->q;
+    a.cnt = c->bcnt + 1;
+    a.scw = c->sc;
+    j.prod[p] = CgProdJob{a, S, 0, 0, ngroups};
+    SymvArgs s1{c->factored ? c->XF : c->M, c->mp, c->m, L.r[(p + 1) & 1],
+                c->factored ? c->ptmp : c->z, c->sc, c->fl, c->bpart, c->bcnt, SYMV_CG_STEP, 0.0,
+                L.r[p], c->q, L.d[p], L.delta, L.q[p], L.q[(p + 1) & 1], c->factored ? 1 : 0, 0};
+    SymvArgs s2{c->XFT, c->mp, c->m, c->ptmp, c->z, c->sc, c->fl, c->bpart, c->bcnt, SYMV_PLAIN,
+                0.0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 1};
+    j.step1[p] = s1;
+    j.step2[p] = s2;
+  }
+  lp_status st = LP_OK;
+  if (!cg_batcher_run(c->batcher, &j, &st)) return LP_OK;
+  *taken = true;
+  ++c->batched_solves;
+  return st;
+}
+
 // PCG from delta = 0 with preconditioner M = Q^{-1} (Alg. 1 step 3), stopping when
 // rho_j = r_j^T M r_j <= min(rel^2 rho_0, abs_thr^2) or after max_iter products.
 //   op 0: (A D^2 A^T) delta = rhs with A streamed in the context's stream dtype;
@@ -1228,10 +1289,20 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
   double* qbuf[2] = {c->qf, c->qf + (size_t)kQCopies * m};
   if (atomic_q) LP_CU(cudaMemsetAsync(c->qf, 0, (size_t)kQCopies * m * sizeof(double), c->st));
   CgLoop L{op, delta, atomic_q, {rbuf[0], rbuf[1]}, {dbuf[0], dbuf[1]}, {qbuf[0], qbuf[1]}};
+  bool finished = false;
+  // a context of the serving loop hands the loop to the batch engine (shared launches)
+  if (c->batcher && op == 0 && atomic_q && c->use_staged && !c->prof_on &&
+      c->stall_group_p1 == 0) {
+    bool taken = false;
+    LP_TRY(cg_batch_solve(c, L, &taken));
+    if (taken) {
+      LP_TRY(sync_scalars(c));
+      finished = c->fl_h[FL_DONE] != 0;
+    }
+  }
   // the device-side loop (one graph launch per solve) once this context has run a CG solve
   // eagerly, with no profiling events or fault injection to honour
-  bool finished = false;
-  if (c->use_graphs && c->prm.use_graphs && c->cg_solves > 0 && !c->prof_on &&
+  if (!finished && c->use_graphs && c->prm.use_graphs && c->cg_solves > 0 && !c->prof_on &&
       c->stall_group_p1 == 0) {
     bool built = false;
     LP_TRY(cg_graph_launch(c, L, max_iter, &built));

@@ -71,6 +71,8 @@ struct CgTune {
 
 }  // namespace lpk
 
+struct CgBatcher;
+
 struct lp_ctx {
   int m = 0;
   int64_t n = 0;
@@ -190,6 +192,10 @@ struct lp_ctx {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
   };
+  // the serving loop's CG batch engine (lp_batch.cu); its CG solves then share launches
+  CgBatcher* batcher = nullptr;
+  cudaEvent_t batch_ready = nullptr;
+  long long batched_solves = 0;
   bool use_graphs = true;      // lp_params.use_graphs and no failure so far
   cudaStream_t cap_st = nullptr;   // private stream the graphs are recorded on (the context
                                    // stream may be the legacy default stream, which cannot be)
@@ -394,6 +400,57 @@ cudaError_t launch_symv_dot(const double* M, int mp, int m, const double* r, dou
                             double* sc, int* fl, double* bpart, unsigned* bcnt, int mode,
                             cudaStream_t st);
 enum SymvMode { SYMV_PLAIN = 0, SYMV_CG_INIT = 1, SYMV_CG_STEP = 2, SYMV_F2 = 3 };
+// Arguments of the preconditioner apply z = M r (k_vec.cu).
+struct SymvArgs {
+  const double* M;
+  int mp, m;
+  const double* r;
+  double* z;
+  double* sc;
+  int* fl;
+  double* bpart;
+  unsigned* bcnt;
+  int mode;
+  double rel2;     // CG relative tolerance squared (CG_INIT)
+  // fused residual update (CG_STEP): r = rold - alpha q; CTA 0 stores r and dy += alpha d
+  const double* rold;
+  const double* q;
+  const double* d;
+  double* dy;
+  const double* qf;    // the product's atomic q copies (q itself holds their sum)
+  double* qzero;       // zeroed by CTA 0 for the next CG product
+  // factored preconditioner M = X^T X (X = L^{-1}, lower triangular): the first of its two
+  // products, t = X r, forms rho = r^T M r as ||t||^2 (sq); the second, z = X^T t, does no
+  // bookkeeping and is skipped once the solve has finished (skip_done)
+  int sq;
+  int skip_done;
+};
+
+// One job of a batched preconditioner apply: one context's rows over CTAs [cta0, cta0 + ncta)
+// of the launch (8 rows per CTA).
+struct SymvJob {
+  SymvArgs a;
+  int cta0, ncta;
+};
+cudaError_t launch_symv_batch(const SymvJob* jobs, int njobs, int total_ctas, size_t smem,
+                              cudaStream_t st);
+
+// One job of a batched CG product (k_cgprod.cu): one context's CG product over CTAs
+// [cta0, cta0 + ncta) of the launch, with S pipeline stages.
+struct CgProdJob {
+  ColArgs a;
+  int S;
+  int cta0, ncta;
+  int64_t ngroups;
+};
+// Shape of one job of a batched CG product: group width tc (8 or 2), warps, stages, dynamic
+// shared memory; false when the matrix is not covered by the batched kernels (more than 16
+// warps of rows).
+bool cgprod_job_shape(lp_dtype ta, int m, int lda, int64_t n, int* tc, int* nwarps, int* S,
+                      int64_t* ngroups, size_t* smem);
+// Launches the batched product over jobs of one (dtype, tc) group; block = nwarps warps.
+cudaError_t launch_cgprod_batch(lp_dtype ta, int tc, const CgProdJob* jobs, int njobs,
+                                int total_ctas, int nwarps, size_t smem, cudaStream_t st);
 // CG step with the residual update fused: r_new = r_old - alpha q staged by every CTA, stored by
 // CTA 0 with dy += alpha d; then z = M r_new, rho = r_new^T z and the CG bookkeeping.
 cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* rold,

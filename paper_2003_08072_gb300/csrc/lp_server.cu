@@ -21,6 +21,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "lp_batch.cuh"
 #include "lp_internal.cuh"
 
 namespace {
@@ -70,6 +71,7 @@ struct lp_server {
   int64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0;
   bool stop = false;
   std::vector<std::thread> workers;
+  CgBatcher* batcher = nullptr;   // shared launches of the live instances' CG iterations
 };
 
 namespace {
@@ -92,6 +94,7 @@ void solve_one(lp_server* sv, Request* r, cudaStream_t st) {
                                r->layout == LP_CSR ? r->indices.data() : nullptr, r->nnz,
                                r->b.data(), r->c.data(), &sv->prm, st);
   if (status == LP_OK) {
+    ctx->batcher = sv->batcher;
     status = lp_ipm_solve(ctx, r->x.data(), r->y.data(), r->s.data(), 0, &r->info);
     if (status != LP_OK) r->error = lp_last_error();
   } else {
@@ -174,6 +177,9 @@ lp_status lp_server_create(lp_server** out, uint64_t mem_budget_bytes, int32_t m
   }
   sv->budget = mem_budget_bytes;
   sv->max_live = max_live;
+  // shared CG launches on request (without the engine, e.g. if its pinned tables cannot be
+  // allocated, every instance runs its own CG loop)
+  if (sv->prm.shared_cg && max_live > 1) sv->batcher = lpk::cg_batcher_create(sv->dev, sv->num_sms);
   try {
     sv->workers.reserve(max_live);
     for (int i = 0; i < max_live; ++i) sv->workers.emplace_back(worker_main, sv.get());
@@ -311,6 +317,10 @@ lp_status lp_server_stats(lp_server* sv, lp_server_stats_t* out) {
   out->mem_in_use = sv->in_use;
   out->mem_peak = sv->peak;
   out->mem_budget = sv->budget;
+  long long rounds = 0, jobs = 0;
+  if (sv->batcher) lpk::cg_batcher_stats(sv->batcher, &rounds, &jobs);
+  out->batched_rounds = rounds;
+  out->batched_cg_solves = jobs;
   return LP_OK;
 }
 
@@ -324,6 +334,7 @@ void lp_server_destroy(lp_server* sv) {
   }
   sv->cv_work.notify_all();
   for (auto& t : sv->workers) t.join();
+  lpk::cg_batcher_destroy(sv->batcher);
   delete sv;
 }
 

@@ -31,24 +31,32 @@ def submit(srv, lp, kind):
                       indices=lp.indices)
 
 
-def alone(lp, kind):
+def alone(lp, kind, prm=None):
     import paper_2003_08072_gb300 as pkg
 
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     if kind == "dense":
-        s = pkg.LPSolver.dense(T(lp.At), T(lp.b), T(lp.c))
+        s = pkg.LPSolver.dense(T(lp.At), T(lp.b), T(lp.c), params=prm)
     else:
         s = pkg.LPSolver.csr(lp.m, lp.n, T(lp.indptr), T(lp.indices), T(lp.values), T(lp.b),
-                             T(lp.c))
+                             T(lp.c), params=prm)
     x, y, sv, info = s.solve()
     s.close()
     return x.cpu().numpy(), info
 
 
-def test_mixed_stream_matches_solves_alone():
+@pytest.mark.parametrize("stream,shared", [("same", 0), ("same", 1), ("bf16", 1)])
+def test_mixed_stream_matches_solves_alone(stream, shared):
+    """Instances overlapping on their own streams, or (shared) with the dense ones' CG
+    iterations in shared launches of the batch engine: every result must still be the
+    instance's own."""
     import paper_2003_08072_gb300 as pkg
 
     pkg.load()
+    prm = pkg.lp_params_default()
+    prm.shared_cg = shared
+    if stream == "bf16":
+        prm.stream_dtype = pkg.LP_BF16
     rng = np.random.default_rng(0)
     reqs = []
     for i in range(24):
@@ -59,7 +67,7 @@ def test_mixed_stream_matches_solves_alone():
     fps = [pkg.lp_footprint_bytes(m, n, pkg.LP_DENSE_COLMAJOR if k == "dense" else pkg.LP_CSR,
                                   pkg.LP_F32, n * max(2, m // 50)) for k, m, n, _ in reqs]
     budget = 3 * max(fps)
-    srv = pkg.LPServer(budget, max_live=6)
+    srv = pkg.LPServer(budget, max_live=6, params=prm)
     inst = {}
     for kind, m, n, seed in reqs:
         lp, A = instance(kind, m, n, seed)
@@ -77,13 +85,20 @@ def test_mixed_stream_matches_solves_alone():
     assert st["completed"] == len(reqs) and st["failed"] == 0 and st["queued"] == 0, st
     assert st["mem_peak"] <= budget
     assert 1 <= st["peak_live"] <= 6
+    if shared:
+        assert st["batched_cg_solves"] > 0 and st["batched_rounds"] > 0, st
+    else:
+        assert st["batched_cg_solves"] == 0, st
     for t, r in got.items():
         kind, lp, A = inst[t]
         assert r["status"] == 0, r["error"]
         assert r["latency_s"] >= r["solve_s"] > 0 and r["queued_s"] >= 0
         x, y, s = r["x"], r["y"], r["s"]
         assert max(iipm.kkt_scaled(A, lp.b, lp.c, x, y, s)) <= 1.01e-8
-        xa, ia = alone(lp, kind)
+        sprm = pkg.lp_params_default()
+        if stream == "bf16" and kind == "dense":
+            sprm.stream_dtype = pkg.LP_BF16
+        xa, ia = alone(lp, kind, sprm)
         oa = float(lp.c @ xa)
         assert abs(float(lp.c @ x) - oa) <= 1e-6 * abs(oa)
         assert abs(r["info"].ipm_iters - ia.ipm_iters) <= 1
