@@ -281,7 +281,10 @@ __device__ __forceinline__ void df_sqrt(float ah, float al, float& h, float& l) 
 }
 
 __device__ __forceinline__ void df_recip(float bh, float bl, float& h, float& l) {
-  const float y = 1.0f / bh;
+  // seed: the hardware's approximate reciprocal (PTX rcp.approx, about 1 ulp); the Newton
+  // step below squares its relative error, as it would that of a correctly rounded seed
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(bh));
   const float p = __fmul_rn(bh, y);
   const float pe = fmaf(bh, y, -p);
   const float e = ((1.0f - p) - pe) - bl * y;   // 1 - (bh + bl) y

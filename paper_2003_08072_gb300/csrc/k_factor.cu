@@ -337,18 +337,26 @@ __device__ __forceinline__ void df_tile_mul(const DFTile& A, const DFTile& B, fl
 // below 1e-14 of the original diagonal entry of Q (q0) counts as lost: returns false.
 //
 // The block is on the factorization's critical path (one per block step), so its dependency
-// chains are kept short.  Pivot p updates a_ij -= a_ip a_jp / a_pp (p < j <= i): each thread
-// loads the inputs of its four elements before it stores any result (so the four chains
-// overlap), 1/a_pp comes from shared memory, and the thread that owns a_{p+1,p+1} forms its
-// reciprocal from the value it just computed, before the one barrier of the step.  Column p is
-// never touched after step p, so after the sweep the lower triangle holds the unscaled
-// columns; square roots and the scaling into L happen afterwards for all columns at once.
-// L^{-1} is formed column by column: the 8 threads of a column sit in one warp and read only
-// their own column, so its rows are ordered by warp barriers alone.
+// chains are kept short and every step does only the work that is live in it.  Pivot p updates
+// a_ij -= a_ip a_jp / a_pp on the trailing triangle p < j <= i; enumerated row by row from its
+// corner (p+1, p+1), that triangle is a prefix of one fixed enumeration of the kNB-1 sized
+// triangle, so each thread keeps the same two slots for the whole sweep and a slot is live
+// while its row index is inside the shrinking triangle.  1/a_pp comes from shared memory, and
+// the thread of slot 0 (which always owns a_{p+1,p+1}) forms the next reciprocal from the value
+// it just computed, before the one barrier of the step.  Column p is never touched after step p,
+// so after the sweep the lower triangle holds the unscaled columns; square roots and the scaling
+// into L happen afterwards for all columns at once.
+// L^{-1} is built by recursive doubling: once the inverses X11, X22 of two neighbouring
+// diagonal blocks of size b are known, the block below them is X21 = -X22 (L21 X11), and all
+// pairs of one level are formed at once: log2(kNB) levels of two small products each, instead
+// of kNB dependent rows.
 __device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl, size_t off, int mp,
                            const double* q0, DFTile& X) {
+  static_assert(kNB == 32, "slot and level layout below assume 32 x 32 blocks and 256 threads");
+  constexpr int kTri = (kNB - 1) * kNB / 2;   // trailing triangle of pivot 0
   __shared__ float rp_h[kNB], rp_l[kNB];   // 1 / (Schur pivot p)
   __shared__ float inv_h[kNB], inv_l[kNB]; // 1 / l_pp
+  __shared__ float w_h[kNB * kNB / 4], w_l[kNB * kNB / 4];   // L21 X11 of one doubling level
   __shared__ int s_ok;
   const int tid = threadIdx.x;
   __shared__ float thr[kNB];                // lost-pivot threshold 1e-14 q0_p (FP32)
@@ -371,43 +379,34 @@ __device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl
     s_ok = 1;
     pivot_recip(0, T.h[0][0], T.l[0][0]);
   }
+  // slot k of this thread: element tid + 256 k of the row-by-row triangle (row ti, column tj)
+  int ti[2], tj[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int e = tid + 256 * k;
+    if (e < kTri) {
+      tri_decode(e, ti[k], tj[k]);
+    } else {
+      ti[k] = kNB;   // never live
+      tj[k] = 0;
+    }
+  }
   __syncthreads();
-  constexpr int K = (kNB * kNB) / 256;   // elements per thread
-  for (int p = 0; p < kNB; ++p) {
+  for (int p = 0; p + 1 < kNB; ++p) {
+    const int live = kNB - 1 - p;   // rows of the trailing triangle
     const float rh = rp_h[p], rl = rp_l[p];
-    float aih[K], ail[K], ajh[K], ajl[K], xh[K], xl[K];
-    bool act[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int e = tid + 256 * k;
-      const int i = e / kNB, j = e % kNB;
-      act[k] = j > p && j <= i;
-      if (act[k]) {
-        aih[k] = T.h[i][p];
-        ail[k] = T.l[i][p];
-        ajh[k] = T.h[j][p];
-        ajl[k] = T.l[j][p];
-        xh[k] = T.h[i][j];
-        xl[k] = T.l[i][j];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (act[k]) {
+    for (int k = 0; k < 2; ++k) {
+      if (ti[k] < live) {
+        const int i = p + 1 + ti[k], j = p + 1 + tj[k];
         float th, tl, h, l;
-        df_mul(aih[k], ail[k], ajh[k], ajl[k], th, tl);
+        df_mul(T.h[i][p], T.l[i][p], T.h[j][p], T.l[j][p], th, tl);
         df_mul(th, tl, rh, rl, h, l);
-        df_add(xh[k], xl[k], -h, -l);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int e = tid + 256 * k;
-      const int i = e / kNB, j = e % kNB;
-      if (act[k]) {
-        T.h[i][j] = xh[k];
-        T.l[i][j] = xl[k];
-        if (i == p + 1 && j == p + 1) pivot_recip(p + 1, xh[k], xl[k]);
+        float xh = T.h[i][j], xl = T.l[i][j];
+        df_add(xh, xl, -h, -l);
+        T.h[i][j] = xh;
+        T.l[i][j] = xl;
+        if (k == 0 && tid == 0) pivot_recip(p + 1, xh, xl);   // slot 0 of thread 0 is (p+1, p+1)
       }
     }
     __syncthreads();
@@ -432,34 +431,35 @@ __device__ bool diag_block(DFTile& T, float* Lh, float* Ll, float* Xh, float* Xl
       T.h[r][cc] = 0.f;
       T.l[r][cc] = 0.f;
     }
+    X.h[r][cc] = (cc == r) ? inv_h[r] : 0.f;
+    X.l[r][cc] = (cc == r) ? inv_l[r] : 0.f;
   }
   __syncthreads();
-  // X = L^{-1}, row by row: X_ij = -inv_ii sum_{j<=q<i} L_iq X_qj (j < i), X_ii = inv_ii;
-  // the 8 threads of column j (one warp) share the sum and reduce with shuffles.
-  const int j = tid >> 3, part = tid & 7;
-  for (int i = 0; i < kNB; ++i) {
-    float s = 0.f, c = 0.f;
-    if (j < i)
-      for (int q = j + part; q < i; q += 8) df_mac(T.h[i][q], T.l[i][q], X.h[q][j], X.l[q][j], s, c);
-#pragma unroll
-    for (int off2 = 4; off2 >= 1; off2 >>= 1)
-      df_add(s, c, __shfl_xor_sync(kFull, s, off2), __shfl_xor_sync(kFull, c, off2));
-    if (part == 0) {
-      float h = 0.f, l = 0.f;
-      if (j < i) {
-        df_mul(s, c, inv_h[i], inv_l[i], h, l);
-        h = -h;
-        l = -l;
-      } else if (j == i) {
-        h = inv_h[i];
-        l = inv_l[i];
-      }
-      X.h[i][j] = h;
-      X.l[i][j] = l;
+  // X = L^{-1}: level b joins pairs of b x b diagonal blocks (s0 = 2b * pair); kNB b / 2 <= 256
+  // elements per level, one per thread
+  for (int b = 1; b < kNB; b <<= 1) {
+    const int ne = kNB * b / 2;
+    const int pair = tid / (b * b), rr = (tid % (b * b)) / b, cc = tid % b, s0 = 2 * b * pair;
+    if (tid < ne) {   // W = L21 X11, X11 lower triangular: q >= cc
+      float s = 0.f, c = 0.f;
+      for (int q = cc; q < b; ++q)
+        df_mac(T.h[s0 + b + rr][s0 + q], T.l[s0 + b + rr][s0 + q], X.h[s0 + q][s0 + cc],
+               X.l[s0 + q][s0 + cc], s, c);
+      fast_two_sum(s, c, w_h[tid], w_l[tid]);
     }
-    __syncwarp();
+    __syncthreads();
+    if (tid < ne) {   // X21 = -X22 W, X22 lower triangular: q <= rr
+      float s = 0.f, c = 0.f;
+      for (int q = 0; q <= rr; ++q)
+        df_mac(X.h[s0 + b + rr][s0 + b + q], X.l[s0 + b + rr][s0 + b + q],
+               w_h[pair * b * b + q * b + cc], w_l[pair * b * b + q * b + cc], s, c);
+      float h, l;
+      fast_two_sum(s, c, h, l);
+      X.h[s0 + b + rr][s0 + cc] = -h;
+      X.l[s0 + b + rr][s0 + cc] = -l;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < kNB * kNB; e += blockDim.x) {
     const int r = e / kNB, cc = e % kNB;
     const size_t a = off + (size_t)r * mp + cc;
