@@ -76,12 +76,15 @@ cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------------------------
-// Iterate preparation: d2 = x/s, d = sqrt(d2); x^T s, c^T x -> mu, sigma mu.
+// Iterate preparation: d2 = x/s, d = sqrt(d2); x^T s, c^T x -> mu, sigma mu.  With dfc, also
+// the double-float pairs of d2, x, 1/s and s - c (four arrays of n) that the FP64-class
+// column passes take their per-column scalars from.
 // ------------------------------------------------------------------------------------
 __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ s, int64_t n,
                        double* __restrict__ d2, double* __restrict__ d, double* sc, double* bpart,
                        unsigned* bcnt, double sigma, const double* __restrict__ c,
-                       float* __restrict__ d2f, const float* __restrict__ cs2) {
+                       float* __restrict__ d2f, const float* __restrict__ cs2,
+                       float2* __restrict__ dfc) {
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -90,6 +93,17 @@ __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ 
     d2[i] = q;
     d[i] = sqrt(q);
     if (d2f) d2f[i] = (float)(cs2 ? q * (double)cs2[i] : q);
+    if (dfc) {
+      float h, l;
+      split_double(q, h, l);
+      dfc[i] = make_float2(h, l);
+      split_double(xi, h, l);
+      dfc[n + i] = make_float2(h, l);
+      split_double(1.0 / si, h, l);
+      dfc[2 * n + i] = make_float2(h, l);
+      split_double(si - c[i], h, l);
+      dfc[3 * n + i] = make_float2(h, l);
+    }
     v[0] += xi * si;
     v[1] += c[i] * xi;
   }
@@ -110,8 +124,9 @@ static int vec_grid(int64_t n) {
 
 cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
                                 double* sc, double* bpart, unsigned* bcnt, double sigma,
-                                const double* c, cudaStream_t st, float* d2f, const float* cs2) {
-  { note_launch(); k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c, d2f, cs2); }
+                                const double* c, cudaStream_t st, float* d2f, const float* cs2,
+                                float2* dfc) {
+  { note_launch(); k_prep<<<vec_grid(n), 256, 0, st>>>(x, s, n, d2, d, sc, bpart, bcnt, sigma, c, d2f, cs2, dfc); }
   return cudaGetLastError();
 }
 

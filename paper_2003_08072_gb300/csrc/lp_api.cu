@@ -198,7 +198,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->colptr);
   dfree(c->rowidx);
   dfree(c->vals);
-  void* bufs[] = {c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
+  void* bufs[] = {c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
@@ -227,6 +227,7 @@ static lp_status alloc_workspace(lp_ctx* c) {
   double** nvec[] = {&c->x, &c->s, &c->d2, &c->d, &c->rd, &c->t, &c->wu, &c->dx, &c->ds};
   for (double** p : nvec) LP_TRY(dalloc(p, (size_t)n));
   LP_TRY(dalloc(&c->d2f, (size_t)n));
+  if (!c->sparse && c->a_dtype == LP_F32) LP_TRY(dalloc(&c->dfc, (size_t)4 * n));
   double** mvec[] = {&c->y, &c->rp, &c->p, &c->dy, &c->r, &c->z, &c->dd, &c->q, &c->rtil,
                      &c->qhat, &c->res, &c->tm, &c->dyacc, &c->rhs, &c->r_alt, &c->d_alt,
                      &c->ptmp};
@@ -628,6 +629,7 @@ static lp_status pass_normal(lp_ctx* c, bool precise, const double* v, const dou
     a.v = v;
     a.d2 = w;
     a.d2f = (!precise && (w == c->d2 || weight_in_d2f)) ? c->d2f : nullptr;
+    a.d2df = (precise && w == c->d2) ? c->dfc : nullptr;
     a.colout = t;
     a.part = c->part;
     a.fl = c->fl;
@@ -785,7 +787,7 @@ static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, cons
                                double sigma, double* rp, double* rd, double* p) {
   PhaseScope ps(c, LP_PH_RESIDUALS);
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, sigma, c->c, c->st,
-                            c->d2f, stream_cs2(c)));
+                            c->d2f, stream_cs2(c), c->dfc));
   int nblk;
   if (!c->sparse) {
     ColArgs a{};
@@ -801,6 +803,13 @@ static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, cons
     a.colout = rd;
     a.part = c->part;
     a.fl = c->fl;
+    a.flw = c->fl;
+    if (c->dfc) {
+      a.d2df = c->dfc;
+      a.xdf = c->dfc + c->n;
+      a.isdf = c->dfc + 2 * c->n;
+      a.scdf = c->dfc + 3 * c->n;
+    }
     nblk = launch_coltile(c->a_dtype, true, MODE_RESID, a, c->num_sms, c->st);
   } else {
     CscArgs a{};
@@ -1582,7 +1591,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
   stream_reset(c);
   const long long graphs0 = c->graph_launches;
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
-                            c->c, c->st, c->d2f, stream_cs2(c)));
+                            c->c, c->st, c->d2f, stream_cs2(c), c->dfc));
   LP_TRY(sync_scalars(c));
   const double mu = c->sc_h[SC_MU];
   if (!(mu > 0) || !isfinite(mu)) return fail(LP_ERR_ARG, "lp_normal_solve: x, s must be positive");
@@ -1698,7 +1707,7 @@ extern "C" lp_status lp_step(lp_ctx* c, double* x, double* y, double* s, const d
   if (!c || !x || !y || !s || !rd || !dy || !Atdy || !Wu) return fail(LP_ERR_ARG, "lp_step: NULL argument");
   if (!(mu0 > 0)) return fail(LP_ERR_ARG, "lp_step: mu0 must be positive");
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
-                            c->c, c->st, c->d2f, stream_cs2(c)));
+                            c->c, c->st, c->d2f, stream_cs2(c), c->dfc));
   (void)mu;  // mu is recomputed from x and s on the device
   LP_TRY(run_step(c, x, y, s, rd, dy, Atdy, Wu, eta, mu0, dx ? dx : c->dx, ds ? ds : c->ds));
   LP_TRY(sync_scalars(c));
@@ -1738,6 +1747,7 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   if (layout != LP_CSR) {
     const int lda = round_up(m, (int)(16 / dtype_size(a_dtype)));
     b += (double)lda * dn * es;
+    if (a_dtype == LP_F32) b += 32 * dn;                                   // column scalars
     if (layout == LP_DENSE_ROWMAJOR) b += dm * dn * es;                    // staging copy
     lp_dtype sd = p.stream_dtype == LP_F64 ? a_dtype : p.stream_dtype;
     if (sd == LP_F64 && a_dtype == LP_F32) sd = LP_F32;

@@ -127,6 +127,9 @@ struct lp_ctx {
   double *x = nullptr, *y = nullptr, *s = nullptr, *d2 = nullptr, *d = nullptr;
   double *rd = nullptr, *t = nullptr, *wu = nullptr, *dx = nullptr, *ds = nullptr;
   float* d2f = nullptr;        // D^2 rounded to FP32 for the FP32-accumulated CG product
+  // dense FP32 A: 4 n double-float pairs D^2, x, 1/s, s - c of the current iterate
+  // (written with d2 by launch_prep_iterate) for the FP64-class passes
+  float2* dfc = nullptr;
   // m-vectors
   double *rp = nullptr, *p = nullptr, *dy = nullptr, *r = nullptr, *z = nullptr, *dd = nullptr;
   double *q = nullptr, *rtil = nullptr, *qhat = nullptr, *res = nullptr, *tm = nullptr;
@@ -270,6 +273,13 @@ struct ColArgs {
   int64_t stall_group_p1;
   // staged CG product only: a launch shape chosen by the autotuner (0: the fixed rule)
   int cfg_tc, cfg_stages, cfg_ctas;
+  // FP64-class passes over an FP32 A: per-column scalars of the iterate as double-float pairs
+  // (written by launch_prep_iterate): NORMAL reads d2df when the weight is D^2; RESID reads
+  // x, 1/s and s - c.  NULL: the scalars are split from the FP64 vectors.
+  const float2* d2df;
+  const float2* xdf;
+  const float2* isdf;
+  const float2* scdf;
 };
 
 
@@ -329,7 +339,7 @@ cudaError_t launch_reduce(const RedArgs& a, cudaStream_t st);
 cudaError_t launch_prep_iterate(const double* x, const double* s, int64_t n, double* d2, double* d,
                                 double* sc, double* bpart, unsigned* bcnt, double sigma,
                                 const double* c, cudaStream_t st, float* d2f = nullptr,
-                                const float* cs2 = nullptr);
+                                const float* cs2 = nullptr, float2* dfc = nullptr);
 cudaError_t launch_d2f(const double* d2, const float* cs2, int64_t n, float* d2f, cudaStream_t st);
 cudaError_t launch_norm2(const double* v, int64_t n, double* sc, int slot, double* bpart,
                          unsigned* bcnt, cudaStream_t st);
