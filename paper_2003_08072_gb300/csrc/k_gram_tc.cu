@@ -361,24 +361,35 @@ __global__ void __launch_bounds__(160, 1) k_gram_tc(GramTcArgs a) {
 }
 
 // Row exponents: e_i with max_k |G_ik| < 2^e_i (from the hi part of the double-float split;
-// 0 for an all-zero or padding row).
-__global__ void k_row_exp(const float* __restrict__ Gh, int ldg, int m, int w, int rows_p,
-                          int* __restrict__ ex) {
+// 0 for an all-zero or padding row).  k_row_max spreads the columns over blockIdx.y and
+// combines the blocks' row maxima with an integer atomic max on the float bits (non-negative
+// floats order like their bit patterns) in ex, zeroed before; k_row_exp turns them into
+// exponents in place.
+__global__ void k_row_max(const float* __restrict__ Gh, int ldg, int m, int w, int* __restrict__ ex) {
   __shared__ float red[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int row = blockIdx.x * 32 + tx;
+  const int per = (w + gridDim.y - 1) / gridDim.y;
+  const int k0 = blockIdx.y * per, k1 = min(w, k0 + per);
   float mx = 0.f;
   if (row < m)
-    for (int k = ty; k < w; k += 8) mx = fmaxf(mx, fabsf(Gh[(size_t)k * ldg + row]));
+    for (int k = k0 + ty; k < k1; k += 8) mx = fmaxf(mx, fabsf(Gh[(size_t)k * ldg + row]));
   red[ty][tx] = mx;
   __syncthreads();
-  if (ty == 0 && row < rows_p) {
+  if (ty == 0 && row < m) {
 #pragma unroll
     for (int j = 1; j < 8; ++j) mx = fmaxf(mx, red[j][tx]);
-    int e = 0;
-    if (mx > 0.f) frexpf(mx, &e);
-    ex[row] = row < m ? e : 0;
+    if (mx > 0.f) atomicMax(&ex[row], __float_as_int(mx));
   }
+}
+
+__global__ void k_row_exp(int m, int rows_p, int* __restrict__ ex) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows_p) return;
+  const float mx = __int_as_float(ex[row]);
+  int e = 0;
+  if (row < m && mx > 0.f) frexpf(mx, &e);
+  ex[row] = row < m ? e : 0;
 }
 
 // Digits of the scaled rows, written in tile order [kb][slice][row group][2][8][8] (k block of
@@ -503,7 +514,15 @@ cudaError_t launch_gram_tc(const float* Gdf, int ldg, int m, int w, int mp, doub
   const int rows_p = gram_tc_rows(m), wp = gram_tc_pitch(w);
   const float* Gh = Gdf;
   const float* Gl = Gdf + (size_t)ldg * w;
-  { note_launch(); k_row_exp<<<rows_p / 32, 256, 0, st>>>(Gh, ldg, m, w, rows_p, ex); }
+  {
+    cudaError_t e0 = cudaMemsetAsync(ex, 0, (size_t)rows_p * sizeof(int), st);
+    if (e0 != cudaSuccess) return e0;
+    const int ysplit = std::max(1, std::min(16, w / 256));
+    note_launch();
+    k_row_max<<<dim3(rows_p / 32, ysplit), 256, 0, st>>>(Gh, ldg, m, w, ex);
+    note_launch();
+    k_row_exp<<<(rows_p + 255) / 256, 256, 0, st>>>(m, rows_p, ex);
+  }
   {
     dim3 grid(wp / 64, rows_p / 32);
     note_launch();

@@ -497,8 +497,13 @@ __global__ void k_step_length(const double* __restrict__ x, const double* __rest
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double xi = x[i], si = s[i], dxi = dx[i], dsi = ds[i];
-    const double r = first_crossing(xi * si - m0, xi * dsi + si * dxi - m1, dxi * dsi - m2);
-    best = fmin(best, r);
+    const double a0 = fmax(xi * si - m0, 0.0), a1 = xi * dsi + si * dxi - m1, a2 = dxi * dsi - m2;
+    // only crossings in (0, 1] can matter (alpha_max <= 1): a0 + min(a1, 0) + min(a2, 0) is a
+    // lower bound of the polynomial on [0, 1], so when it clears its own rounding error the
+    // element has no crossing there and the square root and divisions are skipped
+    const double lb = a0 + fmin(a1, 0.0) + fmin(a2, 0.0);
+    if (lb > 1e-14 * (a0 + fabs(a1) + fabs(a2))) continue;
+    best = fmin(best, first_crossing(a0, a1, a2));
   }
   if (grid_min_last(best, bpart, bcnt) && threadIdx.x == 0) {
     const double eta = sc[SC_ETA], mu0 = sc[SC_MU0];
