@@ -32,37 +32,68 @@ __global__ void __launch_bounds__(512) k_csc(CscArgs a) {
   if constexpr (MODE == MODE_RESID) sigmu = a.sc[SC_SIGMU];
   const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
   const int nwarps = blockDim.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * nwarps + (threadIdx.x >> 5);
+  int64_t gw = (int64_t)blockIdx.x * nwarps + (threadIdx.x >> 5);
   const int64_t tw = (int64_t)gridDim.x * nwarps;
-  for (int64_t cb = gw * 4; cb < a.n; cb += tw * 4) {
-    const int64_t col = cb + grp;
+  // Columns are short (a few nonzeros each), so a group's work is one round trip to memory
+  // per column: the next column's pointers are loaded while the current one is processed,
+  // the lane's first nonzero (value, row) stays in registers from the dot to the scatter,
+  // and the column's scalars are loaded together with its nonzeros.
+  int64_t col = gw * 4 + grp;
+  int64_t k0 = 0, k1 = 0;
+  if (col < a.n) {
+    k0 = a.colptr[col];
+    k1 = a.colptr[col + 1];
+  }
+  for (; gw * 4 < a.n; gw += tw, col += tw * 4) {
     const bool valid = col < a.n;
-    const int64_t k0 = valid ? a.colptr[col] : 0, k1 = valid ? a.colptr[col + 1] : 0;
-    ACC dot = (ACC)0;
-    for (int64_t k = k0 + gl; k < k1; k += 8) dot = fma((ACC)vals[k], vs[a.rowidx[k]], dot);
+    const int64_t ncol = col + tw * 4;
+    int64_t nk0 = 0, nk1 = 0;
+    if (ncol < a.n) {
+      nk0 = a.colptr[ncol];
+      nk1 = a.colptr[ncol + 1];
+    }
+    const bool has0 = valid && k0 + gl < k1;
+    const ACC v0 = has0 ? (ACC)vals[k0 + gl] : (ACC)0;
+    const int r0 = has0 ? a.rowidx[k0 + gl] : 0;
+    double w = 1.0, xi = 0.0, si = 1.0, ci = 0.0;
+    if (valid) {
+      if constexpr (MODE == MODE_NORMAL) {
+        if (a.d2) w = a.d2[col];
+      } else {
+        xi = a.x[col];
+        si = a.s[col];
+        ci = a.c[col];
+      }
+    }
+    ACC dot = has0 ? v0 * vs[r0] : (ACC)0;
+    for (int64_t k = k0 + gl + 8; k < k1; k += 8) dot = fma((ACC)vals[k], vs[a.rowidx[k]], dot);
     dot += __shfl_xor_sync(kFull, dot, 4);
     dot += __shfl_xor_sync(kFull, dot, 2);
     dot += __shfl_xor_sync(kFull, dot, 1);
-    ACC cf[NOUT];
     if (valid) {
+      ACC cf[NOUT];
       if constexpr (MODE == MODE_NORMAL) {
-        const double w = a.d2 ? a.d2[col] : 1.0;
         cf[0] = (ACC)(w * (double)dot);
         if (a.colout && gl == 0) a.colout[col] = (double)dot;
       } else {
-        const double xi = a.x[col], si = a.s[col];
-        const double rdv = (double)dot + si - a.c[col];
+        const double rdv = (double)dot + si - ci;
         cf[0] = (ACC)xi;
         cf[1] = (ACC)(sigmu / si + (xi / si) * rdv);
         if (gl == 0) a.colout[col] = rdv;
       }
-      for (int64_t k = k0 + gl; k < k1; k += 8) {
+      if (has0) {
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) atomicAdd(&ys[o * a.m + r0], cf[o] * v0);
+      }
+      for (int64_t k = k0 + gl + 8; k < k1; k += 8) {
         const int r = a.rowidx[k];
         const ACC av = (ACC)vals[k];
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) atomicAdd(&ys[o * a.m + r], cf[o] * av);
       }
     }
+    k0 = nk0;
+    k1 = nk1;
   }
   __syncthreads();
   ACC* part = reinterpret_cast<ACC*>(a.part);
@@ -72,7 +103,7 @@ __global__ void __launch_bounds__(512) k_csc(CscArgs a) {
       part[((size_t)blockIdx.x * NOUT + o) * a.m + i] = ys[o * a.m + i];
 }
 
-int csc_max_grid(int num_sms) { return num_sms * 2; }
+int csc_max_grid(int num_sms) { return num_sms * 4; }
 
 template <typename TV, typename ACC, int MODE>
 static int launch_csc_t(CscArgs a, int num_sms, cudaStream_t st) {
@@ -82,7 +113,7 @@ static int launch_csc_t(CscArgs a, int num_sms, cudaStream_t st) {
   auto kern = k_csc<TV, ACC, MODE>;
   if (ensure_dyn_smem((const void*)kern, smem) != cudaSuccess) return -1;
   int per_sm = occupancy_cached((const void*)kern, 512, smem);
-  if (per_sm > 2) per_sm = 2;
+  if (per_sm > 4) per_sm = 4;   // the partials buffer holds csc_max_grid rows
   int64_t grid = (int64_t)num_sms * per_sm;
   const int64_t need = (a.n + 63) / 64;
   if (grid > need) grid = need;
