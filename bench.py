@@ -83,6 +83,10 @@ def parse_args():
     ap.add_argument("--sketch", choices=["sparse", "gaussian"], default="sparse",
                     help="sparse sign sketch with --sketch-s nonzeros per row, or Gaussian")
     ap.add_argument("--cg-batch", type=int, default=4)
+    ap.add_argument("--cg-max-iter", type=int, default=None,
+                    help="cap on CG iterations per solve (default: the library's, 500)")
+    ap.add_argument("--study-sketches", type=str, default=None,
+                    help="sketch study: comma-separated subset of s values to run (e.g. '1')")
     ap.add_argument("--no-gram-tc", action="store_true",
                     help="Gram product of the factor in double-float on the FP32 pipes instead "
                          "of the tensor cores")
@@ -369,6 +373,8 @@ def run_ours(args, rank, world, local):
     prm.sketch_s = args.sketch_s
     prm.sketch_kind = 1 if args.sketch == "gaussian" else 0
     prm.cg_batch = args.cg_batch
+    if args.cg_max_iter:
+        prm.cg_max_iter = args.cg_max_iter
     prm.use_graphs = 0 if args.no_graphs else 1
     prm.gram_tensor_cores = 0 if args.no_gram_tc else 1
     prm.autotune = 0 if args.no_autotune else 1
@@ -844,9 +850,14 @@ def run_sketch_study(args, rank, world, local):
                 ("sparse sign s=4", B.LP_SKETCH_SPARSE, 4), ("sparse sign s=8", B.LP_SKETCH_SPARSE, 8)]
     if 8.0 * m * m * n <= 3e11:   # the Gaussian A D W costs 2 m n w = 8 m^2 n flops per IPM iteration
         variants.append(("Gaussian", B.LP_SKETCH_GAUSSIAN, 4))
+    if args.study_sketches:
+        keep = {int(v) for v in args.study_sketches.split(",")}
+        variants = [v for v in variants if v[1] == B.LP_SKETCH_SPARSE and v[2] in keep]
     rows = []
     for name, kind, ns in variants:
         prm = pkg.lp_params_default()
+        if args.cg_max_iter:
+            prm.cg_max_iter = args.cg_max_iter
         prm.sketch_kind = kind
         prm.sketch_s = ns
         prm.sketch_w = (4 * m + ns - 1) // ns * ns      # w = 4m, rounded up to a multiple of s

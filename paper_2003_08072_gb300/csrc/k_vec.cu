@@ -392,6 +392,11 @@ __global__ void k_vec_ops(int op, double* a, const double* b, const double* c, i
       case VOP_SUB: a[i] = b[i] - c[i]; break;
       case VOP_NEG: a[i] = -b[i]; break;
       case VOP_ONES: a[i] = 1.0; break;
+      case VOP_SIGNS: {   // sign from the top bit of a multiplicative hash of i
+        const unsigned h = ((unsigned)i + 1u) * 0x9E3779B1u;
+        a[i] = ((h ^ (h >> 15)) & 0x8000u) ? -1.0 : 1.0;
+        break;
+      }
     }
   }
 }

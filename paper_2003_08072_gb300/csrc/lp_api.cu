@@ -885,7 +885,10 @@ static lp_status run_gram(lp_ctx* c, const float* Gdf) {
 
 // Probe check of a factor stage: ||(Q + eps diag Q)(M 1) - 1|| / sqrt(m) and the pivot flag.
 static lp_status factor_check(lp_ctx* c, double eps, double* qerr, bool* brk) {
-  LP_CU(launch_vec_ops(VOP_ONES, c->res, nullptr, nullptr, c->m, nullptr, c->st));
+  // a fixed +-1 probe has a component ~1/sqrt(m) along every eigenvector of Q, so an inverse
+  // that is wrong along a few directions of a numerically singular Q (CountSketch) shows; the
+  // all-ones vector can miss them
+  LP_CU(launch_vec_ops(VOP_SIGNS, c->res, nullptr, nullptr, c->m, nullptr, c->st));
   LP_CU(launch_symv_dot(c->M, c->mp, c->m, c->res, c->tm, c->sc, c->fl, c->bpart, c->bcnt,
                         SYMV_PLAIN, c->st));
   LP_CU(launch_symv_f64(c->Q, c->mp, c->m, c->tm, c->rhs, c->st));

@@ -486,7 +486,9 @@ int coltile_max_grid(int num_sms);
 int csc_max_grid(int num_sms);
 cudaError_t launch_vec_ops(int op, double* a, const double* b, const double* c, int m,
                            const double* sc, cudaStream_t st);
-enum VecOp { VOP_COPY = 0, VOP_ZERO = 1, VOP_ADD = 2, VOP_SUB = 3, VOP_NEG = 4, VOP_ONES = 5 };
+// VOP_SIGNS: a fixed pseudo-random +-1 vector (the factor's quality probe)
+enum VecOp { VOP_COPY = 0, VOP_ZERO = 1, VOP_ADD = 2, VOP_SUB = 3, VOP_NEG = 4, VOP_ONES = 5,
+             VOP_SIGNS = 6 };
 
 // IPM update
 cudaError_t launch_update_dirs(const double* x, const double* s, const double* d2, const double* d,
