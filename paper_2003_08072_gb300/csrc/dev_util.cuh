@@ -233,6 +233,30 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   lo = (float)(x - (double)hi);
 }
 
+// The same split from the bits of x, on the integer and FP32 pipes (the FP64 conversions of
+// split_double run on this GPU's slow FP64 units): hi is x rounded to 24 significant bits by
+// adding half a unit of the 29 dropped mantissa bits to the bit pattern and clearing them (a
+// carry into the exponent field is the correct rounding), lo the signed remainder
+// (|lo| <= 2^28 units of 2^(e-1075), rounded to FP32), so hi + lo is within 2^-49 of x, as
+// with split_double.  Inputs outside 2^-70 < |x| < 2^100 (and zero) take split_double.
+__device__ __forceinline__ void split_double_bits(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);   // biased exponent
+  if (e < 1023 - 70 || e > 1023 + 100) {
+    split_double(x, hi, lo);
+    return;
+  }
+  const unsigned long long bh = (b + (1ull << 28)) & ~((1ull << 29) - 1ull);
+  const int eh = (int)((bh >> 52) & 0x7ff);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  hi = __uint_as_float(sign | ((unsigned)(eh - 1023 + 127) << 23) |
+                       (unsigned)((bh >> 29) & 0x7fffffu));
+  const float rem = __int2float_rn((int)(long long)(b - bh));   // |b - bh| <= 2^28
+  // 2^(e-1075) is a normal float for e >= 950
+  const float scaled = rem * __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+  lo = sign ? -scaled : scaled;
+}
+
 // (s, c) += a * (bh + bl).  The leading product is rounded on its own (__fmul_rn is never
 // contracted into an FMA), so that p + pe == a * bh exactly and TwoSum sees the rounded p.
 __device__ __forceinline__ void df_fma(float a, float bh, float bl, float& s, float& c) {

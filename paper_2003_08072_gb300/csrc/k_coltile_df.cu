@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(512) k_coltile_df(ColArgs a) {
           x = a.v[row];
         }
       }
-      split_double(x, vh[sl][e], vl[sl][e]);
+      split_double_bits(x, vh[sl][e], vl[sl][e]);
 #pragma unroll
       for (int o = 0; o < NOUT; ++o) ys[o][sl][e] = yc[o][sl][e] = 0.f;
     }
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colwarp_df(ColArgs a) {
           x = a.v[r];
         }
       }
-      split_double(x, vh[r], vl[r]);
+      split_double_bits(x, vh[r], vl[r]);
     }
   }
   float smh = 0.f, sml = 0.f;   // RESID: sigma mu

@@ -95,13 +95,13 @@ __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ 
     if (d2f) d2f[i] = (float)(cs2 ? q * (double)cs2[i] : q);
     if (dfc) {
       float h, l;
-      split_double(q, h, l);
+      split_double_bits(q, h, l);
       dfc[i] = make_float2(h, l);
-      split_double(xi, h, l);
+      split_double_bits(xi, h, l);
       dfc[n + i] = make_float2(h, l);
-      split_double(1.0 / si, h, l);
+      split_double_bits(1.0 / si, h, l);
       dfc[2 * n + i] = make_float2(h, l);
-      split_double(si - c[i], h, l);
+      split_double_bits(si - c[i], h, l);
       dfc[3 * n + i] = make_float2(h, l);
     }
     v[0] += xi * si;
@@ -176,13 +176,32 @@ __device__ __forceinline__ void symv_body(const SymvArgs& a, int bid, int nblk) 
   float* rh = reinterpret_cast<float*>(rs + m4);      // DF: r split into hi / lo floats
   float* rl = rh + m4;
   const double al = a.rold ? a.sc[SC_ALPHA] : 0.0;
-  for (int i = threadIdx.x; i < m4; i += blockDim.x) {
-    double v = 0.0;
-    if (i < a.m) {
-      if (a.rold) {
-        // with atomic copies the product's last CTA has already summed them into q
-        const double qi = a.q[i];
-        v = fma(-al, qi, a.rold[i]);
+  // a thread's loads of q and r_old are all issued before any of its stores
+  constexpr int kU = 4;
+  for (int base = threadIdx.x; base < m4; base += kU * blockDim.x) {
+    double qv[kU], rv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * blockDim.x;
+      qv[u] = 0.0;
+      rv[u] = 0.0;
+      if (i < a.m) {
+        if (a.rold) {
+          // with atomic copies the product's last CTA has already summed them into q
+          qv[u] = a.q[i];
+          rv[u] = a.rold[i];
+        } else {
+          rv[u] = a.r[i];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i >= m4) continue;
+      double v = rv[u];
+      if (a.rold && i < a.m) {
+        v = fma(-al, qv[u], rv[u]);
         if (bid == 0) {
           const_cast<double*>(a.r)[i] = v;
           a.dy[i] = fma(al, a.d[i], a.dy[i]);
@@ -190,12 +209,10 @@ __device__ __forceinline__ void symv_body(const SymvArgs& a, int bid, int nblk) 
 #pragma unroll
             for (int k = 0; k < kQCopies; ++k) a.qzero[(size_t)k * a.m + i] = 0.0;
         }
-      } else {
-        v = a.r[i];
       }
+      rs[i] = v;
+      if (DF) split_double_bits(v, rh[i], rl[i]);
     }
-    rs[i] = v;
-    if (DF) split_double(v, rh[i], rl[i]);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -213,7 +230,7 @@ __device__ __forceinline__ void symv_body(const SymvArgs& a, int bid, int nblk) 
       const float4* rl4 = reinterpret_cast<const float4*>(rl);
       const int n4 = m4 >> 2;
       float s = 0.f, c = 0.f;
-#pragma unroll 4
+#pragma unroll 8
       for (int j = lane; j < n4; j += 32) {
         const float4 mh = __ldcg(Mh + j), ml = __ldcg(Ml + j);
         const float4 xh = rh4[j], xl = rl4[j];
