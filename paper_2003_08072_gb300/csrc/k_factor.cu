@@ -23,7 +23,7 @@ __global__ void k_split_df(const double* __restrict__ G, size_t count, float* __
                            float* __restrict__ Gl) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x)
-    split_double(G[i], Gh[i], Gl[i]);
+    split_double_bits(G[i], Gh[i], Gl[i]);
 }
 
 // One 64 x 64 lower tile of G G^T over a slice of the w columns, in double-float arithmetic on
@@ -480,7 +480,7 @@ __global__ void k_q_to_df(const double* __restrict__ Q, int mp, int m, double ep
     double v = Q[i];
     const size_t r = i / mp, cc = i % mp;
     if (r == cc && (int)r < m) v *= (1.0 + eps);
-    split_double(v, Ah[i], Al[i]);
+    split_double_bits(v, Ah[i], Al[i]);
   }
 }
 
@@ -676,7 +676,7 @@ cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double
 // Q (FP64, mp x mp) -> M = (Q + eps diag Q)^{-1} as DF pairs in M's storage (Mh = (float*)M,
 // Ml = Mh + mp^2); X (same size) is work space for L^{-1}.
 cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
-                                int* fl, cudaStream_t st) {
+                                int* fl, cudaStream_t st, bool form_m) {
   const int nbk = mp / kNB;
   const size_t mm = (size_t)mp * mp;
   float* Ah = reinterpret_cast<float*>(M);
@@ -694,7 +694,7 @@ cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, 
     const int nupd = r * (r + 1) / 2 + r * (kb + 1);
     if (nupd > 0) { note_launch(); k_ch_update<<<nupd, 256, 0, st>>>(Ah, Al, Xh, Xl, Q0, mp, nbk, kb, fl); }
   }
-  { note_launch(); k_ch_xtx<<<nbk * (nbk + 1) / 2, 256, 0, st>>>(Xh, Xl, Ah, Al, mp, nbk, fl); }
+  if (form_m) { note_launch(); k_ch_xtx<<<nbk * (nbk + 1) / 2, 256, 0, st>>>(Xh, Xl, Ah, Al, mp, nbk, fl); }
   return cudaGetLastError();
 }
 

@@ -99,7 +99,7 @@ __global__ void k_scatter(const int32_t* hb, int64_t n, int s, const int32_t* st
     if (coef) {
       const double v = (h < 0 ? -d[col] : d[col]) * inv_sqrt_s;
       float ch, cl;
-      split_double(v, ch, cl);
+      split_double_bits(v, ch, cl);
       coef[pos] = make_float2(ch, cl);
     }
   }

@@ -198,7 +198,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->colptr);
   dfree(c->rowidx);
   dfree(c->vals);
-  void* bufs[] = {c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
+  void* bufs[] = {c->Mf64, c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
@@ -883,6 +883,39 @@ static lp_status run_gram(lp_ctx* c, const float* Gdf) {
   return LP_OK;
 }
 
+// Whether M = X^T X can come from the tensor-core Gram product with the context's buffers
+// (sized for the m x w sketch; X^T is m x mp).
+static bool xtx_on_tensor_cores(const lp_ctx* c) {
+  return c->prm.gram_tensor_cores && gram_tc_digit_bytes(c->m, c->mp) <= gram_tc_digit_bytes(c->m, c->w) &&
+         gram_tc_part_bytes(c->m, c->mp, c->mp, c->num_sms) <=
+             gram_tc_part_bytes(c->m, c->mp, c->w, c->num_sms);
+}
+
+// M = X^T X for X = L^{-1} (double-float, row-major mp x mp in c->X; rows and columns past m
+// are the identity): the Gram product of the columns of X on the tensor cores -- X's hi and lo
+// planes, read column-major with leading dimension mp, are X^T -- into FP64, then split into
+// M's double-float planes.
+static lp_status form_m_tensor_cores(lp_ctx* c) {
+  const size_t mm = (size_t)c->mp * c->mp;
+  if (!c->Mf64) {
+    AllocStream as(c->st);
+    LP_TRY(dalloc(&c->Mf64, mm));
+  }
+  LP_CU(launch_gram_tc(reinterpret_cast<const float*>(c->X), c->mp, c->m, c->mp, c->mp, c->Mf64,
+                       c->gdig, c->gex, c->gpart, c->num_sms, c->fl, c->st));
+  LP_CU(launch_split_df(c->Mf64, mm, reinterpret_cast<float*>(c->M), c->st));
+  return LP_OK;
+}
+
+// Cholesky factor and inverse of (Q + eps diag Q) with M = X^T X (form_m) on the tensor cores
+// when the buffers allow, else in the factor's own double-float kernel.
+static lp_status chol_inverse(lp_ctx* c, double eps, bool form_m) {
+  const bool tc = form_m && xtx_on_tensor_cores(c);
+  LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps, c->fl, c->st, form_m && !tc));
+  if (tc) LP_TRY(form_m_tensor_cores(c));
+  return LP_OK;
+}
+
 // Probe check of a factor stage: ||(Q + eps diag Q)(M 1) - 1|| / sqrt(m) and the pivot flag.
 static lp_status factor_check(lp_ctx* c, double eps, double* qerr, bool* brk) {
   // a fixed +-1 probe has a component ~1/sqrt(m) along every eigenvector of Q, so an inverse
@@ -944,7 +977,7 @@ static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
   double qerr = 0.0;
   bool brk = false;
   LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
-  LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, 0.0, c->fl, c->st));
+  LP_TRY(chol_inverse(c, 0.0, true));
   LP_TRY(factor_check(c, 0.0, &qerr, &brk));
   c->qerr = qerr;
   c->shift = 0.0;
@@ -957,7 +990,7 @@ static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
   double eps1 = 1e-10;
   for (;;) {
     LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
-    LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps1, c->fl, c->st));
+    LP_TRY(chol_inverse(c, eps1, false));   // stage 1 needs X1 = L1^{-1} only
     LP_TRY(sync_scalars(c));
     if (!c->fl_h[FL_BREAK]) break;
     eps1 *= 100.0;
@@ -990,7 +1023,7 @@ static lp_status run_factor(lp_ctx* c, const double* G, bool allow_shift) {
   double eps = 0.0;
   for (;;) {
     LP_CU(launch_set(nullptr, 0, 0.0, c->fl, FL_BREAK, 0, c->st));
-    LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps, c->fl, c->st));
+    LP_TRY(chol_inverse(c, eps, true));
     LP_TRY(factor_check(c, eps, &qerr, &brk));
     if (!brk && qerr < 0.5) break;
     eps = eps > 0.0 ? eps * 100.0 : 1e-10;
@@ -1740,7 +1773,7 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   b += (double)std::max(coltile_max_grid(num_sms), csc_max_grid(num_sms)) * 2 * dm * 8;
   b += dn * s * (4 + 4 + 8) + 2.0 * kQCopies * dm * 8 + 3.0 * (w + 1) * 4; // sketch indices, q
   b += (double)round_up(m, 2) * w * 16 + (double)w * 8;                    // G, its split, u
-  b += 3.0 * mp * mp * 8;                                                  // Q, M, X
+  b += 4.0 * mp * mp * 8;                                                  // Q, M, X, M in FP64
   b += (double)gram_split_cap(m, w, num_sms) * (nt * (nt + 1) / 2) * 64.0 * 64.0 * 8;
   b += (double)gram_tc_digit_bytes(m, w) + 4.0 * gram_tc_rows(m) +
        (double)gram_tc_part_bytes(m, mp, w, num_sms);                      // tensor-core Gram

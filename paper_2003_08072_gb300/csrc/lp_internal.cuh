@@ -172,6 +172,7 @@ struct lp_ctx {
   bool factored = false;       // the preconditioner is applied as XF^T (XF r)
   int factor_stages = 1;       // stages of the last factorization (1 or 2)
   double qerr = 0.0;           // probe error ||Q M 1 - 1|| / sqrt(m) of the last factor stage
+  double* Mf64 = nullptr;       // M = X^T X in FP64 from the tensor-core Gram (first use)
   double* X1 = nullptr;
   double* XF = nullptr;
   double* XFT = nullptr;
@@ -398,8 +399,9 @@ struct TrmmArgs {
 cudaError_t launch_df_trmm(const TrmmArgs& a, cudaStream_t st);
 cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double eps,
                              const double* v, cudaStream_t st);
+// form_m = false skips M = X^T X (the caller forms it, or needs only X).
 cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
-                                int* fl, cudaStream_t st);
+                                int* fl, cudaStream_t st, bool form_m = true);
 cudaError_t launch_df_to_double(const double* Mdf, int mp, int m, double* out, int ld,
                                 cudaStream_t st);
 cudaError_t launch_symv_f64(const double* M, int mp, int m, const double* r, double* z,
