@@ -92,6 +92,8 @@ def parse_args():
                          "of the tensor cores")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed launch-shape rule for the CG product instead of the autotuner")
+    ap.add_argument("--persistent", action="store_true",
+                    help="run CG solves as one persistent cooperative launch each (lp_params.persistent_cg)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven CG loop instead of one CUDA graph launch per CG solve")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -376,6 +378,7 @@ def run_ours(args, rank, world, local):
     if args.cg_max_iter:
         prm.cg_max_iter = args.cg_max_iter
     prm.use_graphs = 0 if args.no_graphs else 1
+    prm.persistent_cg = 1 if args.persistent else 0
     prm.gram_tensor_cores = 0 if args.no_gram_tc else 1
     prm.autotune = 0 if args.no_autotune else 1
     sparse = args.workload == "sparse"
@@ -496,7 +499,8 @@ def run_ours(args, rank, world, local):
             "tol": prm.tol, "sigma": prm.sigma, "gamma": prm.gamma,
             "l2": "inputs larger than L2 (A is %.0f MB)" % (a_bytes / 1e6),
             "parallelism": f"replicas x{world}",
-            "cg_loop": "host-driven" if args.no_graphs else "CUDA graph per CG solve",
+            "cg_loop": ("persistent cooperative launch per CG solve" if args.persistent else
+                        "host-driven" if args.no_graphs else "CUDA graph per CG solve"),
             "gram": ("double-float, FP32 pipes" if args.no_gram_tc else
                      "tensor cores (tcgen05, exact BF16 digit slices)"),
         },
@@ -529,6 +533,7 @@ def run_ours(args, rank, world, local):
         "ipm_iters_per_lp": ipm_iters,
         "cg_iters_per_lp": cg_total,
         "cg_graph_solves_per_lp": statistics.mean(i.cg_graph_solves for i in infos),
+        "cg_persistent_solves_per_lp": statistics.mean(i.cg_persistent_solves for i in infos),
         "objective": obj,
         "kkt": max(infos[-1].rp_rel, infos[-1].rd_rel, infos[-1].gap_rel),
         "phase_ms_per_lp": prof.as_dict()["phase_ms"],

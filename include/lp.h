@@ -107,6 +107,12 @@ typedef struct {
                             iterations share launches through the server's batch engine; 0 = each
                             instance runs its own CG loop (one CUDA graph launch per CG solve, the
                             instances overlapping on their own streams) (0) */
+  int32_t persistent_cg; /* 1 = the CG loop over a dense A streamed below FP64 (m <= 4096) runs as
+                            one cooperative launch per CG solve, products and preconditioner applies
+                            separated by bounded grid barriers; 0 = CUDA graph (use_graphs) or host
+                            loop.  Measured on GB300 no faster than the graph launches (slower for
+                            m <= 300: the kernel holds both phases' registers, so fewer CTAs stream
+                            the product).  A serving loop with max_live > 1 sets it to 0 (0) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */
@@ -132,6 +138,8 @@ typedef struct {
                                  products stopped contracting on the master copy itself; -1 if never */
   int32_t cg_graph_solves;    /* CG solves of this call that ran as one CUDA graph launch each
                                  (lp_params.use_graphs) */
+  int32_t cg_persistent_solves; /* CG solves of this call that ran as one persistent cooperative
+                                   launch each (lp_params.persistent_cg) */
 } lp_info;
 
 /* Fills *prm with the defaults listed above.  LP_ERR_ARG if prm is NULL. */

@@ -44,6 +44,7 @@ class lp_params(ctypes.Structure):
         ("gram_tensor_cores", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("shared_cg", ctypes.c_int32),
+        ("persistent_cg", ctypes.c_int32),
     ]
 
 
@@ -69,6 +70,7 @@ class lp_info(ctypes.Structure):
         ("factor_two_stage", ctypes.c_int32),
         ("cg_precise_iter", ctypes.c_int32),
         ("cg_graph_solves", ctypes.c_int32),
+        ("cg_persistent_solves", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -43,6 +43,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// Ends an mbarrier's life (no pending arrivals or copies), so its shared memory may be reused.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Makes mbarrier initialisations visible to the other threads and to the async proxy.
 __device__ __forceinline__ void fence_mbarrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -69,6 +74,52 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     if (mbar_try_wait(bar, parity)) return true;
     if ((spin & 255u) == 0 && global_ns() - t0 > limit_ns) return false;
   }
+}
+
+// Barrier over all CTAs of a cooperative launch (every CTA resident), in two levels so that no
+// single counter takes every arrival: CTA b arrives on counter 2 + (b % kBarFan); the last of
+// each group arrives on bar[0]; the last of those bumps the generation word bar[1], on which
+// the others wait (polling with a short back-off).  bar holds 2 + kBarFan zeroed words at
+// launch.  The wait is bounded by the global timer; false when it gave up (the caller reports
+// a timeout and stops).
+constexpr int kBarFan = 16;
+
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, uint64_t limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    const unsigned nb = gridDim.x, b = blockIdx.x;
+    const unsigned grp = b % kBarFan;
+    const unsigned ngrp = nb < (unsigned)kBarFan ? nb : (unsigned)kBarFan;
+    const unsigned in_grp = nb / kBarFan + (grp < nb % kBarFan ? 1u : 0u);
+    __threadfence();
+    bool last = false;
+    if (atomicAdd(&bar[2 + grp], 1u) == in_grp - 1) {
+      atomicExch(&bar[2 + grp], 0u);
+      __threadfence();
+      last = atomicAdd(&bar[0], 1u) == ngrp - 1;
+    }
+    if (last) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      for (unsigned spin = 1; *gen == g; ++spin) {
+        __nanosleep(32);
+        if ((spin & 63u) == 0 && global_ns() - t0 > limit_ns) {
+          s_ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 }  // namespace lpk

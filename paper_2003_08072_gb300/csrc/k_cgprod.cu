@@ -30,6 +30,7 @@
 
 #include "bulk_util.cuh"
 #include "dev_util.cuh"
+#include "symv_body.cuh"
 
 namespace lpk {
 
@@ -37,9 +38,11 @@ namespace lpk {
 // Shared memory: S stages of TC * lda elements, then S mbarriers.  The body runs as block bid
 // of a grid of nblk blocks: the whole launch (k_cgprod) or one job's share of a batched launch
 // (k_cgprod_batch).
+// inval: end the stage mbarriers' lives before returning (the persistent CG loop reuses their
+// shared memory for the preconditioner apply and initialises them again next iteration).
 template <typename TA, int SPW, int TC, bool KEEP>
 __device__ __forceinline__ void cgprod_body(const ColArgs& a, int S, int64_t ngroups, int bid,
-                                            int nblk) {
+                                            int nblk, bool inval = false) {
   constexpr int VEC = VecN<TA>::N;
   constexpr bool COMP = sizeof(TA) == 4;   // compensated row sums for FP32 copies
   extern __shared__ __align__(128) unsigned char smem[];
@@ -220,6 +223,11 @@ __device__ __forceinline__ void cgprod_body(const ColArgs& a, int S, int64_t ngr
       }
     }
     __syncthreads();
+  }
+  if (inval) {
+    __syncthreads();   // every wait on the stage barriers is over
+    if (threadIdx.x == 0)
+      for (int s = 0; s < S; ++s) mbar_inval(&bars[s]);
   }
   auto row_sum = [&](int sl, int e) -> double {
     if constexpr (COMP) return (double)yr[sl][e] + (double)yc[sl][e];
@@ -444,6 +452,136 @@ int tune_cgprod(lp_dtype ta, ColArgs a, int num_sms, int max_grid, cudaStream_t 
 }
 
 // ---- batched CG products (the serving loop's shared launches) --------------------------
+
+// ---- persistent CG loop ----------------------------------------------------------------
+// One CTA (the product's warps, one row slice each) runs, per iteration, its share of the CG
+// product (cgprod_body as block b of the whole grid) and, for the first ceil(m / warps) CTAs,
+// one row per warp of the preconditioner apply (symv_body); grid barriers order the product's q and alpha before the apply, and the apply's
+// r, z, rho and beta before the next product.  After each iteration every CTA reads the stop
+// flag (set by the apply's last CTA: converged, iteration cap, non-finite) and the timeout flag.
+// The two bodies share the dynamic shared memory; the product ends its mbarriers' lives first.
+template <typename TA, int SPW, int TC, bool KEEP>
+__global__ void __launch_bounds__(256) k_cg_persistent(CgPersistArgs p, int S, int64_t ngroups,
+                                                        int nblk_symv) {
+  const uint64_t lim = p.wait_ns ? p.wait_ns : kWaitLimitNs;
+  for (int j = 0; j < p.max_trips; ++j) {
+    const int par = j & 1;
+    cgprod_body<TA, SPW, TC, KEEP>(p.prod[par], S, ngroups, blockIdx.x, gridDim.x, true);
+    bool ok = grid_sync_bounded(p.bar, lim);
+    if (ok) {
+      if ((int)blockIdx.x < nblk_symv) symv_body<true>(p.step1[par], blockIdx.x, nblk_symv);
+      if (p.factored) {
+        ok = grid_sync_bounded(p.bar, lim);
+        if (ok && (int)blockIdx.x < nblk_symv) symv_body<true>(p.step2[par], blockIdx.x, nblk_symv);
+      }
+    }
+    if (ok) ok = grid_sync_bounded(p.bar, lim);
+    if (!ok) {
+      if (threadIdx.x == 0) p.fl[FL_TIMEOUT] = 1;
+      return;
+    }
+    const int done = *reinterpret_cast<volatile int*>(&p.fl[FL_DONE]);
+    const int to = *reinterpret_cast<volatile int*>(&p.fl[FL_TIMEOUT]);
+    if (done || to) return;
+  }
+}
+
+namespace {
+
+template <typename TA, int SPW, int TC>
+int launch_cg_persistent_t(CgPersistArgs p, int nwarps, int num_sms, cudaStream_t st) {
+  constexpr bool KEEP = keep_default<TA>() && SPW == 1;
+  const ColArgs& a = p.prod[0];
+  const size_t stage = (size_t)TC * a.lda * sizeof(TA);
+  const size_t symv_bytes = (size_t)((a.m + 3) & ~3) * 2 * sizeof(double);
+  const int threads = 32 * nwarps;
+  const int nblk_symv = (a.m + nwarps - 1) / nwarps;   // one row of the apply per warp
+  const int64_t ngroups = (a.n + TC - 1) / TC;
+  auto kern = k_cg_persistent<TA, SPW, TC, KEEP>;
+  // as many CTAs per SM (up to 8) as registers and shared memory allow, with 3-4 stages where
+  // that still gives every row of the apply a warp, else with 2
+  int per_sm = 0, S = 0;
+  size_t smem = 0;
+  for (int min_s = 3; min_s >= 2 && !per_sm; --min_s) {
+    for (int k = 8; k >= 1; --k) {
+      const int s_k = (int)std::min<size_t>(4, (kSmemBudget / k) / (stage + 8));
+      if (s_k < min_s) continue;
+      const size_t sm_k = std::max((size_t)s_k * stage + (size_t)s_k * 8, symv_bytes);
+      if (ensure_dyn_smem((const void*)kern, sm_k) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+      }
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, sm_k) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+      }
+      if (occ < k || (int64_t)num_sms * k < nblk_symv) continue;
+      per_sm = k;
+      S = s_k;
+      smem = sm_k;
+      break;
+    }
+  }
+  if (!per_sm) return -1;   // the apply's rows cannot all be co-resident
+  {
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (grid > ngroups) grid = std::max<int64_t>(ngroups, nblk_symv);
+    int Si = S;
+    int64_t ng = ngroups;
+    int nb = nblk_symv;
+    void* args[] = {&p, &Si, &ng, &nb};
+    note_launch();
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid),
+                                                      dim3(threads), args, smem, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    return (int)grid;
+  }
+}
+
+template <typename TA>
+int launch_cg_persistent_dt(CgPersistArgs p, int num_sms, cudaStream_t st) {
+  constexpr int VEC = VecN<TA>::N;
+  const ColArgs& a = p.prod[0];
+  const int nslices = (a.m + 32 * VEC - 1) / (32 * VEC);
+  const bool wide = (size_t)8 * a.lda * sizeof(TA) > 64 * 1024;
+  // the product's own warps (one row slice each, up to 8): the block size of both phases
+  if (nslices <= 8)
+    return wide ? launch_cg_persistent_t<TA, 1, 2>(p, nslices, num_sms, st)
+                : launch_cg_persistent_t<TA, 1, 8>(p, nslices, num_sms, st);
+  if (nslices <= 16)
+    return wide ? launch_cg_persistent_t<TA, 2, 2>(p, (nslices + 1) / 2, num_sms, st)
+                : launch_cg_persistent_t<TA, 2, 8>(p, (nslices + 1) / 2, num_sms, st);
+  if (nslices <= 32)
+    return wide ? launch_cg_persistent_t<TA, 4, 2>(p, (nslices + 3) / 4, num_sms, st)
+                : launch_cg_persistent_t<TA, 4, 8>(p, (nslices + 3) / 4, num_sms, st);
+  return -1;
+}
+
+}  // namespace
+
+int launch_cg_persistent(lp_dtype ta, CgPersistArgs p, int num_sms, cudaStream_t st) {
+  static int coop = -1;   // device attribute, read once per process
+  if (coop < 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    coop = v;
+  }
+  if (!coop || p.prod[0].m > 4096) return -1;
+  switch (ta) {
+    case LP_F32: return launch_cg_persistent_dt<float>(p, num_sms, st);
+    case LP_BF16: return launch_cg_persistent_dt<__nv_bfloat16>(p, num_sms, st);
+    case LP_F16: return launch_cg_persistent_dt<__half>(p, num_sms, st);
+    default: return -1;
+  }
+}
 
 bool cgprod_job_shape(lp_dtype ta, int m, int lda, int64_t n, int* tc, int* nwarps, int* S,
                       int64_t* ngroups, size_t* smem) {

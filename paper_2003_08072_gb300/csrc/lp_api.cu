@@ -90,6 +90,7 @@ lp_status lp_params_default(lp_params* p) {
   p->gram_tensor_cores = 1;
   p->autotune = 1;
   p->shared_cg = 0;
+  p->persistent_cg = 0;
   return LP_OK;
 }
 
@@ -198,7 +199,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->colptr);
   dfree(c->rowidx);
   dfree(c->vals);
-  void* bufs[] = {c->Mf64, c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
+  void* bufs[] = {c->pbar, c->Mf64, c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
@@ -263,6 +264,7 @@ static lp_status alloc_workspace(lp_ctx* c) {
   LP_TRY(dalloc(&c->gex, (size_t)gram_tc_rows(m)));
   LP_TRY(dalloc((unsigned char**)&c->gpart, gram_tc_part_bytes(m, c->mp, c->w, c->num_sms)));
   // scalars
+  LP_TRY(dalloc(&c->pbar, 32));
   LP_TRY(dalloc(&c->sc, SC_COUNT));
   LP_TRY(dalloc(&c->fl, FL_COUNT));
   LP_TRY(dalloc(&c->bpart, (size_t)kMaxRedBlocks * 8));
@@ -1249,6 +1251,54 @@ static lp_status cg_graph_launch(lp_ctx* c, const CgLoop& L, int max_iter, bool*
 // Runs the CG loop of L (op 0, staged FP32-accumulated product) in the serving loop's batch
 // engine: the launch descriptors of both iteration parities, exactly those cg_iteration would
 // launch, go into a job.  *taken is false when the matrix or the engine cannot take it.
+// The CG loop of a dense A streamed below FP64 as one cooperative launch (k_cg_persistent):
+// every iteration's product and preconditioner apply in one kernel, with the argument sets of
+// the serving engine's jobs.  ran = false when the launch does not cover the shape.
+static lp_status cg_persistent_solve(lp_ctx* c, const CgLoop& L, int max_iter, bool* ran) {
+  *ran = false;
+  CgPersistArgs p{};
+  for (int q = 0; q < 2; ++q) {
+    ColArgs a{};
+    a.A = c->As;
+    a.lda = c->lda_s;
+    a.m = c->m;
+    a.n = c->n;
+    a.d2 = c->d2;
+    a.d2f = c->d2f;
+    a.part = c->part;
+    a.fl = c->fl;
+    a.sc = c->sc;
+    a.skip_if_done = 1;
+    a.dz = c->z;
+    a.dold = L.d[(q + 1) & 1];
+    a.dnew = L.d[q];
+    a.flw = c->fl;
+    a.qacc = L.q[q];
+    a.qsum = c->q;
+    a.cnt = c->bcnt + 1;
+    a.scw = c->sc;
+    p.prod[q] = a;
+    p.step1[q] = SymvArgs{c->factored ? c->XF : c->M, c->mp, c->m, L.r[(q + 1) & 1],
+                          c->factored ? c->ptmp : c->z, c->sc, c->fl, c->bpart, c->bcnt,
+                          SYMV_CG_STEP, 0.0, L.r[q], c->q, L.d[q], L.delta, L.q[q],
+                          L.q[(q + 1) & 1], c->factored ? 1 : 0, 0};
+    p.step2[q] = SymvArgs{c->XFT, c->mp, c->m, c->ptmp, c->z, c->sc, c->fl, c->bpart, c->bcnt,
+                          SYMV_PLAIN, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                          0, 1};
+  }
+  p.factored = c->factored ? 1 : 0;
+  p.bar = c->pbar;
+  p.fl = c->fl;
+  p.wait_ns = 0;
+  p.max_trips = max_iter + 4;   // the apply sets the stop flag at max_iter
+  LP_CU(cudaMemsetAsync(c->pbar, 0, 32 * sizeof(unsigned), c->st));
+  if (launch_cg_persistent(c->s_dtype, p, c->num_sms, c->st) < 0) return LP_OK;
+  LP_CU(cudaGetLastError());
+  *ran = true;
+  ++c->persistent_launches;
+  return LP_OK;
+}
+
 static lp_status cg_batch_solve(lp_ctx* c, const CgLoop& L, bool* taken) {
   *taken = false;
   int tc = 8, nwarps = 1, S = 3;
@@ -1343,6 +1393,19 @@ static lp_status run_pcg(lp_ctx* c, int op, const double* rhs, double* delta, do
     if (taken) {
       LP_TRY(sync_scalars(c));
       finished = c->fl_h[FL_DONE] != 0;
+    }
+  }
+  // the persistent loop (one cooperative launch per solve), with no profiling events or fault
+  // injection to honour
+  if (!finished && c->prm.persistent_cg && op == 0 && atomic_q && c->use_staged && !c->prof_on &&
+      c->stall_group_p1 == 0) {
+    bool ran = false;
+    LP_TRY(cg_persistent_solve(c, L, max_iter, &ran));
+    if (ran) {
+      LP_TRY(sync_scalars(c));
+      if (!c->fl_h[FL_DONE])
+        return fail(LP_ERR_CUDA, "persistent CG loop ended without its stop flag");
+      finished = true;
     }
   }
   // the device-side loop (one graph launch per solve) once this context has run a CG solve
@@ -1498,7 +1561,7 @@ static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_
   const int m = c->m;
   const int64_t n = c->n;
   lp_info inf{};
-  const long long graphs0 = c->graph_launches;
+  const long long graphs0 = c->graph_launches, pers0 = c->persistent_launches;
   if (resume && resume->stream_switch_iter >= 0) stream_switch(c, resume->stream_switch_iter);
   if (start_given) {
     LP_CU(cudaMemcpyAsync(c->x, x, n * sizeof(double), cudaMemcpyDefault, c->st));
@@ -1584,6 +1647,7 @@ static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_
   inf.stream_switch_iter = c->switch_iter;
   inf.cg_precise_iter = c->precise_iter;
   inf.cg_graph_solves = (int32_t)(c->graph_launches - graphs0);
+  inf.cg_persistent_solves = (int32_t)(c->persistent_launches - pers0);
   c->ipm_state.k = k;
   c->ipm_state.stream_switch_iter = c->switch_iter;
   c->ipm_state.r0 = r0;
@@ -1625,7 +1689,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
   if (!c || !x || !s || !p || !dy) return fail(LP_ERR_ARG, "lp_normal_solve: NULL argument");
   if (k < 0) return fail(LP_ERR_ARG, "lp_normal_solve: k < 0");
   stream_reset(c);
-  const long long graphs0 = c->graph_launches;
+  const long long graphs0 = c->graph_launches, pers0 = c->persistent_launches;
   LP_CU(launch_prep_iterate(x, s, c->n, c->d2, c->d, c->sc, c->bpart, c->bcnt, c->prm.sigma,
                             c->c, c->st, c->d2f, stream_cs2(c), c->dfc));
   LP_TRY(sync_scalars(c));
@@ -1658,6 +1722,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
     inf.factor_two_stage = c->factor_stages == 2 ? 1 : 0;
     inf.cg_precise_iter = c->precise_iter;
     inf.cg_graph_solves = (int32_t)(c->graph_launches - graphs0);
+    inf.cg_persistent_solves = (int32_t)(c->persistent_launches - pers0);
     *info = inf;
   }
   return LP_OK;

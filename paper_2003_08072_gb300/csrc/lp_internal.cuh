@@ -207,6 +207,8 @@ struct lp_ctx {
   long long cg_solves = 0;     // CG solves run (the first one always runs eagerly)
   std::vector<CgGraph> cg_graphs;
   long long graph_launches = 0;
+  long long persistent_launches = 0;
+  unsigned* pbar = nullptr;     // grid barrier words of the persistent CG loop (32)
 
   // profiling (CUDA events on st)
   struct EvPair {
@@ -463,6 +465,24 @@ bool cgprod_job_shape(lp_dtype ta, int m, int lda, int64_t n, int* tc, int* nwar
 // Launches the batched product over jobs of one (dtype, tc) group; block = nwarps warps.
 cudaError_t launch_cgprod_batch(lp_dtype ta, int tc, const CgProdJob* jobs, int njobs,
                                 int total_ctas, int nwarps, size_t smem, cudaStream_t st);
+// Persistent CG loop (k_cgprod.cu): one cooperative launch runs CG iterations j = 0, 1, ... until
+// the device stop flag, iteration j being the CG product prod[j & 1] and the preconditioner
+// apply step1[j & 1] (then step2[j & 1] for the two-stage factor), separated by bounded grid
+// barriers (bar: 2 + kBarFan zeroed words, see bulk_util.cuh).  The argument sets are those of the serving engine's jobs.
+struct CgPersistArgs {
+  ColArgs prod[2];
+  SymvArgs step1[2], step2[2];
+  int factored;
+  unsigned* bar;
+  int* fl;
+  uint64_t wait_ns;    // limit of each wait (0: 1 s)
+  int max_trips;       // iterations at most (the stop flag ends the loop before)
+};
+// Runs the loop for a dense A streamed in FP32/BF16/FP16 with m <= 4096 (rows of the product in
+// at most 8 warps, one row of the apply per warp covered by the grid); -1 when not covered or
+// the device cannot launch it cooperatively.  Returns the grid size.
+int launch_cg_persistent(lp_dtype ta, CgPersistArgs p, int num_sms, cudaStream_t st);
+
 // CG step with the residual update fused: r_new = r_old - alpha q staged by every CTA, stored by
 // CTA 0 with dy += alpha d; then z = M r_new, rho = r_new^T z and the CG bookkeeping.
 cudaError_t launch_symv_cg_step(const double* M, int mp, int m, const double* rold,

@@ -168,6 +168,9 @@ lp_status lp_server_create(lp_server** out, uint64_t mem_budget_bytes, int32_t m
     return LP_ERR_OOM;
   }
   if (prm) sv->prm = *prm; else lp_params_default(&sv->prm);
+  // a persistent CG loop holds every SM for its solve, which would serialise the live
+  // instances: with several of them each runs its CG solves as CUDA graph launches instead
+  if (max_live > 1) sv->prm.persistent_cg = 0;
   if (cudaGetDevice(&sv->dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->dev) !=
           cudaSuccess) {

@@ -14,11 +14,11 @@ STRUCTS = {
     "lp_params": ["tol", "cg_rel_tol", "sigma", "gamma", "cg_max_iter", "ipm_max_iter",
                   "refine_max", "sketch_s", "sketch_w", "cg_theory_rule", "seed", "stream_dtype",
                   "cg_batch", "inner_solver", "sketch_kind", "use_graphs",
-                  "gram_tensor_cores", "autotune", "shared_cg"],
+                  "gram_tensor_cores", "autotune", "shared_cg", "persistent_cg"],
     "lp_info": ["ipm_iters", "cg_iters_total", "cg_iters_last", "refine_steps", "rp_rel",
                 "rd_rel", "gap_rel", "mu", "obj", "alpha_max", "alpha", "f_norm", "v_norm",
                 "status", "f_target", "stream_dtype", "stream_switch_iter", "factor_two_stage",
-                "cg_precise_iter", "cg_graph_solves"],
+                "cg_precise_iter", "cg_graph_solves", "cg_persistent_solves"],
     "lp_ipm_state": ["k", "stream_switch_iter", "r0", "mu0"],
     "lp_profile": ["phase_ms", "phase_calls", "matvec_ms", "matvec_count", "matvec_bytes",
                    "launches", "tune_tc", "tune_stages", "tune_ctas", "tune_us", "tune_rule_us"],

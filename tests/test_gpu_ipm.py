@@ -206,7 +206,7 @@ def test_graph_captured_cg_matches_eager(case):
         else:
             dt = np.float64 if case == "dense_f64" or case == "countsketch" else np.float32
             lp = synth.dense_lp(3, 80, 6000, dtype=dt)
-            prm = params(use_graphs=graphs, sketch_s=1 if case == "countsketch" else 4,
+            prm = params(use_graphs=graphs, persistent_cg=0, sketch_s=1 if case == "countsketch" else 4,
                          stream_dtype=pkg.LP_BF16 if case == "dense_bf16" else pkg.LP_F64)
             s = pkg.LPSolver.dense(T(lp.At), T(lp.b), T(lp.c), params=prm)
         x, y, sv, info = s.solve()
@@ -218,3 +218,32 @@ def test_graph_captured_cg_matches_eager(case):
     assert abs(ig.ipm_iters - ie.ipm_iters) <= 1
     assert abs(og - oe) <= 1e-6 * abs(oe)
     assert max(ig.rp_rel, ig.rd_rel, ig.gap_rel) <= 1e-8
+
+
+@pytest.mark.parametrize("case", ["dense_f32", "dense_bf16", "countsketch_f32", "wide_m"])
+def test_persistent_cg_matches_eager(case):
+    """The persistent CG loop (one cooperative launch per CG solve: the products and the
+    preconditioner applies of all iterations in one kernel, separated by grid barriers) against
+    the host-driven loop: same IPM iteration count within one, same objective to 1e-6, both to
+    scaled KKT 1e-8; the persistent run really ran its CG solves that way.  CountSketch brings
+    in the two-stage preconditioner (two applies per iteration), m = 1100 two row slices per
+    warp in the product."""
+    import paper_2003_08072_gb300 as pkg
+
+    m, n = (1100, 12000) if case == "wide_m" else (80, 6000)
+    lp = synth.dense_lp(5, m, n, dtype=np.float32)
+    out = {}
+    for pers in (1, 0):
+        prm = params(use_graphs=0, persistent_cg=pers,
+                     sketch_s=1 if case == "countsketch_f32" else 4,
+                     stream_dtype=pkg.LP_BF16 if case == "dense_bf16" else pkg.LP_F64)
+        s = pkg.LPSolver.dense(T(lp.At), T(lp.b), T(lp.c), params=prm)
+        x, y, sv, info = s.solve()
+        out[pers] = (float(lp.c @ x.cpu().numpy()), info)
+        s.close()
+    (op_, ip), (oe, ie) = out[1], out[0]
+    assert ip.status == 0 and ie.status == 0
+    assert ip.cg_persistent_solves > 0 and ie.cg_persistent_solves == 0
+    assert abs(ip.ipm_iters - ie.ipm_iters) <= 1
+    assert abs(op_ - oe) <= 1e-6 * abs(oe)
+    assert max(ip.rp_rel, ip.rd_rel, ip.gap_rel) <= 1e-8
