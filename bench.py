@@ -30,10 +30,10 @@ if ROOT not in sys.path:
 
 # DRAM bytes of one CG product launch from an ncu capture of the same kernel source
 # (k_cgprod.cu at the recorded hash); reported only while the kernel source is unchanged.
-NCU_TRAFFIC = {"source_sha1": "6528766d8ab0ea89832ebfe8f8c83d75835a4310",
-               "bytes_per_launch": 803.96e6,
-               "case": "dense m=1000 n=200000 FP32, ncu --set full (profiles/k_cgprod_cg_product_"
-                       "dense_m1000_n200000_f32.md)"}
+NCU_TRAFFIC = {"source_sha1": "7c8ddb492c5bed03423d805db0fe9600dce4135b",
+               "bytes_per_launch": 803.94e6,
+               "case": "dense m=1000 n=200000 FP32, ncu --metrics dram__bytes_read.sum,"
+                       "dram__bytes_write.sum (profiles/k_cgprod_cg_product_dense_m1000_n200000_f32.md)"}
 
 
 def parse_args():
