@@ -105,7 +105,37 @@ __global__ void k_scatter(const int32_t* hb, int64_t n, int s, const int32_t* st
   }
 }
 
-cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, const int32_t* start,
+// Members of each bucket in column order.  The scatter places them through an atomic cursor, so
+// their order -- and with it the rounding of each bucket's sum in the gather -- would change from
+// run to run.  One CTA per bucket ranks its members by column index (distinct within a bucket:
+// the s nonzeros of a column lie in s different buckets) and writes them back in that order.
+// A bucket of more than kSortCap members (far beyond n s / w on any sketch used here) keeps the
+// scatter's order.
+constexpr int kSortCap = 2048;
+
+__global__ void __launch_bounds__(256) k_sort_buckets(const int32_t* __restrict__ start,
+                                                      int32_t* __restrict__ list,
+                                                      float2* __restrict__ coef) {
+  __shared__ int32_t key[kSortCap];
+  __shared__ float2 cf[kSortCap];
+  const int b = blockIdx.x;
+  const int32_t s0 = start[b], len = start[b + 1] - s0;
+  if (len <= 1 || len > kSortCap) return;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    key[i] = list[s0 + i];
+    if (coef) cf[i] = coef[s0 + i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const int32_t ki = key[i] & 0x7fffffff;
+    int r = 0;
+    for (int j = 0; j < len; ++j) r += (key[j] & 0x7fffffff) < ki;
+    list[s0 + r] = key[i];
+    if (coef) coef[s0 + r] = cf[i];
+  }
+}
+
+cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, int w, const int32_t* start,
                                   int32_t* cursor, int32_t* list, const double* d, float2* coef,
                                   cudaStream_t st) {
   const int64_t total = n * (int64_t)s;
@@ -113,6 +143,7 @@ cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, const int
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
   { note_launch(); k_scatter<<<(unsigned)grid, 256, 0, st>>>(hb, n, s, start, cursor, list, d, coef); }
+  { note_launch(); k_sort_buckets<<<(unsigned)w, 256, 0, st>>>(start, list, coef); }
   return cudaGetLastError();
 }
 

@@ -862,7 +862,7 @@ static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
   LP_CU(cudaMemsetAsync(c->cnt, 0, (c->w + 1) * sizeof(int32_t), c->st));
   LP_CU(launch_sketch_hash(c->prm.seed, k, c->n, c->ss, c->w, c->hb, c->cnt, nullptr, nullptr, c->st));
   LP_CU(launch_sketch_scan(c->cnt, c->w, c->start, c->cursor, c->st));
-  LP_CU(launch_sketch_scatter(c->hb, c->n, c->ss, c->start, c->cursor, c->list, d, c->coef,
+  LP_CU(launch_sketch_scatter(c->hb, c->n, c->ss, c->w, c->start, c->cursor, c->list, d, c->coef,
                               c->st));
   if (!c->sparse) {
     LP_CU(launch_sketch_gather_dense(c->a_dtype, c->A, c->lda, c->m, c->ss, c->w, c->start,

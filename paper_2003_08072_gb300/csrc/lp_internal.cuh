@@ -352,7 +352,8 @@ cudaError_t launch_sketch_hash(uint64_t seed, int k, int64_t n, int s, int w, in
                                int32_t* cnt, int32_t* bucket_out, int8_t* sign_out, cudaStream_t st);
 cudaError_t launch_sketch_scan(const int32_t* cnt, int w, int32_t* start, int32_t* cursor,
                                cudaStream_t st);
-cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, const int32_t* start,
+// (followed by an order of each bucket's members by column index, so G is reproducible)
+cudaError_t launch_sketch_scatter(const int32_t* hb, int64_t n, int s, int w, const int32_t* start,
                                   int32_t* cursor, int32_t* list, const double* d, float2* coef,
                                   cudaStream_t st);
 cudaError_t launch_sketch_gather_dense(lp_dtype ta, const void* A, int64_t lda, int m, int s,

@@ -20,6 +20,31 @@ __device__ __forceinline__ void symv_body(const SymvArgs& a, int bid, int nblk) 
   float* rh = reinterpret_cast<float*>(rs + m4);      // DF: r split into hi / lo floats
   float* rl = rh + m4;
   const double al = a.rold ? a.sc[SC_ALPHA] : 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = bid * (int)(blockDim.x >> 5) + warp;
+  const int n4 = m4 >> 2;
+  // DF: the first kPre chunks of this warp's row of M do not depend on the CG step, so they are
+  // loaded before r is staged and their latency hides behind it
+  constexpr int kPre = 8;
+  float4 pmh[DF ? kPre : 1], pml[DF ? kPre : 1];
+  const float4* Mh = nullptr;
+  const float4* Ml = nullptr;
+  if constexpr (DF) {
+    Mh = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.M) + (size_t)row * a.mp);
+    Ml = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.M) +
+                                         (size_t)a.mp * a.mp + (size_t)row * a.mp);
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int j = lane + 32 * k;
+      if (row < a.m && j < n4) {
+        pmh[k] = __ldcg(Mh + j);
+        pml[k] = __ldcg(Ml + j);
+      } else {
+        pmh[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pml[k] = pmh[k];
+      }
+    }
+  }
   // a thread's loads of q and r_old are all issued before any of its stores
   constexpr int kU = 4;
   for (int base = threadIdx.x; base < m4; base += kU * blockDim.x) {
@@ -59,23 +84,27 @@ __device__ __forceinline__ void symv_body(const SymvArgs& a, int bid, int nblk) 
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row = bid * (int)(blockDim.x >> 5) + warp;
   double dotc = 0.0;
   if (row < a.m) {
     double acc;
     if constexpr (DF) {
-      // 16-byte loads of the row's hi and lo parts: every load of a row is in flight at once
-      const float4* Mh = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.M) +
-                                                         (size_t)row * a.mp);
-      const float4* Ml = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.M) +
-                                                         (size_t)a.mp * a.mp + (size_t)row * a.mp);
       const float4* rh4 = reinterpret_cast<const float4*>(rh);
       const float4* rl4 = reinterpret_cast<const float4*>(rl);
-      const int n4 = m4 >> 2;
       float s = 0.f, c = 0.f;
+#pragma unroll
+      for (int k = 0; k < kPre; ++k) {
+        const int j = lane + 32 * k;
+        if (j < n4) {
+          const float4 mh = pmh[k], ml = pml[k];
+          const float4 xh = rh4[j], xl = rl4[j];
+          df_mac(mh.x, ml.x, xh.x, xl.x, s, c);
+          df_mac(mh.y, ml.y, xh.y, xl.y, s, c);
+          df_mac(mh.z, ml.z, xh.z, xl.z, s, c);
+          df_mac(mh.w, ml.w, xh.w, xl.w, s, c);
+        }
+      }
 #pragma unroll 8
-      for (int j = lane; j < n4; j += 32) {
+      for (int j = lane + 32 * kPre; j < n4; j += 32) {
         const float4 mh = __ldcg(Mh + j), ml = __ldcg(Ml + j);
         const float4 xh = rh4[j], xl = rl4[j];
         df_mac(mh.x, ml.x, xh.x, xl.x, s, c);
