@@ -426,18 +426,11 @@ def run_ours(args, rank, world, local):
     launches = pkg.lp_profile_read(ctx).launches - launches0
     # one more solve, untimed, with CUDA events on the library's stream around every phase and
     # every CG product: the per-launch duration of the CG product and the phase split
-    # (the host-driven loop of a profiled solve checks the stop flag every 32 CG iterations, so
-    # that each product's events bracket the kernel rather than the host's launch gap after a
-    # check; products queued past the stop are not counted)
-    prm_prof = type(prm).from_buffer_copy(prm)
-    prm_prof.cg_batch = 32
-    pkg.lp_set_params(ctx, prm_prof)
     pkg.lp_profile_enable(ctx, True)
     pkg.lp_profile_read(ctx, reset=True)
     pkg.lp_ipm_solve(ctx, x, y, s)
     prof = pkg.lp_profile_read(ctx)
     pkg.lp_profile_enable(ctx, False)
-    pkg.lp_set_params(ctx, prm)
     obj = float(torch.dot(c_dev, x))
     pkg.lp_destroy(ctx)
     del keep
@@ -529,8 +522,7 @@ def run_ours(args, rank, world, local):
             "launches": int(prof.matvec_count),
             "timing": "CUDA events on the library's stream around every CG product of one "
                       "profiled LP solve run after the timed steps (the timed steps run without "
-                      "events; the profiled solve's host loop checks the stop flag every 32 CG "
-                      "iterations)",
+                      "events)",
             "autotune": prof.as_dict()["tune"],
         },
         "e2e": {"value": (world * k_e2e / e2e_t) if k_e2e else None, "unit": "LP/s",
