@@ -291,7 +291,7 @@ lp_status lp_sketch(lp_ctx* ctx, const double* d, int32_t k, double* G);
  *   Minv : device m*m float64 output or NULL (symmetric).
  * LP_ERR_BREAKDOWN if a pivot is not positive (rank(G) < m).  Synchronous.
  * Inside lp_ipm_solve and lp_normal_solve, a Q that is numerically singular for this explicit
- * inverse (a lost pivot, or ||Q Minv 1 - 1|| / sqrt(m) >= 1e-2; CountSketch reaches
+ * inverse (a lost pivot, or ||Q Minv z - z|| / sqrt(m) >= 1e-2 for a fixed +-1 probe z; CountSketch reaches
  * kappa(Q) ~ 1e17 late in the IPM) is factored in two stages instead: a shifted Cholesky
  * factor L1 of Q whitens G into G1 = L1^{-1} G, a second Cholesky factor L2 of G1 G1^T
  * follows, and the preconditioner is applied as X^T (X r) with X = L2^{-1} L1^{-1}, whose
