@@ -113,6 +113,12 @@ typedef struct {
                             loop.  Measured on GB300 no faster than the graph launches (slower for
                             m <= 300: the kernel holds both phases' registers, so fewer CTAs stream
                             the product).  A serving loop with max_live > 1 sets it to 0 (0) */
+  int32_t factor_dag;    /* 1: the blocked Cholesky sweep of the factor (Alg. 1 step 2) runs as one
+                            launch whose CTAs claim its 32 x 32 tile products in dependency order,
+                            waiting on per-tile counters (bounded waits: LP_ERR_TIMEOUT), so that only
+                            the diagonal blocks' pivot chains are sequential; same arithmetic, bitwise
+                            the same factor as 0: two launches per block step.  m above 8192 always
+                            takes the block-step launches (1) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */

@@ -45,6 +45,7 @@ class lp_params(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("shared_cg", ctypes.c_int32),
         ("persistent_cg", ctypes.c_int32),
+        ("factor_dag", ctypes.c_int32),
     ]
 
 

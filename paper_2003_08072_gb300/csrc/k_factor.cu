@@ -9,6 +9,9 @@
 //      row-major mp x mp matrix (identity on the padding).
 //   2. Q^{-1} = L^{-T} L^{-1} from a blocked Cholesky factor Q = L L^T (Q is symmetric positive
 //      definite when rank(A D W) = m, Lemma 4.1); a lost pivot flags a numerically singular Q.
+#include <algorithm>
+
+#include "bulk_util.cuh"
 #include "dev_util.cuh"
 
 namespace lpk {
@@ -311,23 +314,25 @@ __device__ __forceinline__ void load_df(DFTile& T, const float* h, const float* 
 
 // out[k] = sum_q A[r][q] * B(q, c) for the 4 elements e = tid + 256 k (r = e / 32, c = e % 32);
 // TRB: B(q, c) = B[c][q] (A B^T), else B[q][c] (A B).  TRA: A(r, q) = A[q][r] (A^T B).
+// The four sums are independent dependency chains; they advance together (q outermost) so
+// that their latencies overlap.  Each sum still takes its terms in the order q = 0, 1, ...
 template <bool TRA, bool TRB>
 __device__ __forceinline__ void df_tile_mul(const DFTile& A, const DFTile& B, float (&s)[4],
                                             float (&c)[4]) {
+  const int cc = threadIdx.x % kNB, r0 = threadIdx.x / kNB;   // rows r0 + 8 k
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int e = threadIdx.x + 256 * k, r = e / kNB, cc = e % kNB;
-    float ss = 0.f, c2 = 0.f;
-#pragma unroll 8
-    for (int q = 0; q < kNB; ++q) {
+  for (int k = 0; k < 4; ++k) s[k] = c[k] = 0.f;
+#pragma unroll 4
+  for (int q = 0; q < kNB; ++q) {
+    const float bh = TRB ? B.h[cc][q] : B.h[q][cc];
+    const float bl = TRB ? B.l[cc][q] : B.l[q][cc];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = r0 + 8 * k;
       const float ah = TRA ? A.h[q][r] : A.h[r][q];
       const float al = TRA ? A.l[q][r] : A.l[r][q];
-      const float bh = TRB ? B.h[cc][q] : B.h[q][cc];
-      const float bl = TRB ? B.l[cc][q] : B.l[q][cc];
-      df_mac(ah, al, bh, bl, ss, c2);
+      df_mac(ah, al, bh, bl, s[k], c[k]);
     }
-    s[k] = ss;
-    c[k] = c2;
   }
 }
 
@@ -612,6 +617,288 @@ __global__ void __launch_bounds__(256) k_ch_update(float* Ah, float* Al, float* 
   if (!ok && threadIdx.x == 0) fl[FL_BREAK] = 1;
 }
 
+// ---- the same sweep as one launch of tile tasks ---------------------------------------------
+//
+// The block-step sweep above is bound by latency, not work: each of its nbk steps is two
+// launches, and the update launch lasts as long as the pivot chain of the next diagonal block.
+// Here the same tile operations are the tasks of one launch.  The sequential part, per block
+// step k
+//   L_{k,k-1} = A_{k,k-1} X_{k-1,k-1}^T,  A_kk -= L_{k,k-1} L_{k,k-1}^T,  factor and invert A_kk,
+// is one task, F, that runs the whole chain in one CTA with X_{k-1,k-1} kept in shared memory.
+// The other CTAs claim the remaining tasks from a counter in a fixed order
+//   T(i,k)    L_ik = A_ik X_kk^T, i >= k + 2;
+//   XS(k,j)   X_kj <- X_kk X_kj, j < k;
+//   U(i,j,k)  A_ij -= L_ik L_jk^T, k < j <= i, except (k+1, k+1) which F does;
+//   XU(i,j,k) X_ij -= L_ik X_kj, i > k >= j,
+// listed block step after block step (S(0), S(1), ...; within S(k) in the order above, with
+// U(k+2,k+1,k) and U(k+2,k+2,k), which F needs next, first).  Every tile has a counter of the
+// operations done on it; a task waits (bounded by the global timer) until the counters of its
+// inputs reach the values it needs, does its tile product and publishes its own counter.
+// Counters (cA for A/L tiles, cX for X tiles, i >= j):
+//   cA[i][j] = number of trailing updates applied (k of them before block step k = j), then
+//              j + 1 once the tile is final (L_ij, or L_jj and X_jj);
+//   cX[i][j] (i > j) = number of updates X_ij -= L_iq X_qj applied (q = j .. i-1), then
+//              i - j + 1 once X_ij is final.
+// Progress: F is claimed first.  A task of S(k) reads F's results up to step k + 1 and tasks
+// listed before it; F's step j reads tasks of S(j - 2) and earlier.  So whenever F waits, the
+// first unfinished task of the list has every input ready and is (or will be) claimed by a
+// running CTA; whenever that task waits, F can advance.  The launch finishes whatever the
+// number of resident CTAs (two or more).  F stays ahead: the two updates it needs at step j
+// can start once step j - 1 has published L_{j-1,j-2}, a whole diagonal factor earlier.
+// Each tile receives the same operations in the same order as in the block-step sweep, in the
+// same arithmetic, so both routes give bitwise the same L and X.  A lost pivot is flagged as
+// there; the sweep runs on with the replaced pivot (finite values) and the caller discards the
+// result.
+enum : uint32_t { CT_F = 0, CT_T = 1, CT_U = 2, CT_XS = 3, CT_XU = 4 };
+
+__host__ __device__ __forceinline__ uint32_t ct_pack(uint32_t kind, int i, int j, int k) {
+  return (kind << 27) | ((uint32_t)i << 18) | ((uint32_t)j << 9) | (uint32_t)k;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait until *cnt >= target.  Gives up (false) when another task has flagged a
+// timeout, or after limit_ns, flagging FL_TIMEOUT itself.
+__device__ bool dag_wait(const int* cnt, int target, int* fl, uint64_t t0, uint64_t limit_ns) {
+  for (unsigned spin = 0;; ++spin) {
+    if (ld_acquire(cnt) >= target) return true;
+    if ((spin & 15u) == 15u) {
+      if (*(volatile int*)&fl[FL_TIMEOUT]) return false;
+      if (global_ns() - t0 > limit_ns) {
+        atomicExch(&fl[FL_TIMEOUT], 1);
+        return false;
+      }
+    }
+    if (spin >= 64) __nanosleep(64);
+  }
+}
+
+// Tile loads through L2 only: a tile read earlier by this SM may have been rewritten since.
+__device__ __forceinline__ void load_df_cg(DFTile& T, const float* h, const float* l, size_t off,
+                                           int ld) {
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    const size_t a = off + (size_t)(e / kNB) * ld + e % kNB;
+    T.h[e / kNB][e % kNB] = __ldcg(h + a);
+    T.l[e / kNB][e % kNB] = __ldcg(l + a);
+  }
+}
+
+// Makes the CTA's global writes visible, then sets *cnt = v (thread 0).
+__device__ __forceinline__ void dag_publish(int* cnt, int v) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(cnt, v);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ch_dag(float* Ah, float* Al, float* Xh, float* Xl,
+                                                const double* __restrict__ Q0, int mp, int nbk,
+                                                const uint32_t* __restrict__ tasks, int ntasks,
+                                                int* sync, int* fl, uint64_t limit_ns) {
+  __shared__ DFTile S1;
+  __shared__ DFTile S2;
+  __shared__ double q0[kNB];
+  __shared__ int s_task, s_ok;
+  int* cA = sync + 2;
+  int* cX = cA + (size_t)nbk * nbk;
+  const int tid = threadIdx.x;
+  auto tile = [&](int i, int j) { return (size_t)(i * kNB) * mp + j * kNB; };
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(&sync[0], 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= ntasks) break;
+    const uint32_t code = tasks[t];
+    const uint32_t kind = code >> 27;
+    const int i = (code >> 18) & 511, j = (code >> 9) & 511, k = code & 511;
+    if (tid == 0) {
+      const uint64_t t0 = global_ns();
+      bool ok = true;
+      switch (kind) {
+        case CT_F:   // waits inside, per block step
+          break;
+        case CT_T:
+          ok = dag_wait(&cA[i * nbk + k], k, fl, t0, limit_ns) &&
+               dag_wait(&cA[k * nbk + k], k + 1, fl, t0, limit_ns);
+          break;
+        case CT_U:
+          ok = dag_wait(&cA[i * nbk + k], k + 1, fl, t0, limit_ns) &&
+               dag_wait(&cA[j * nbk + k], k + 1, fl, t0, limit_ns) &&
+               dag_wait(&cA[i * nbk + j], k, fl, t0, limit_ns);
+          break;
+        case CT_XS:
+          ok = dag_wait(&cA[k * nbk + k], k + 1, fl, t0, limit_ns) &&
+               dag_wait(&cX[k * nbk + j], k - j, fl, t0, limit_ns);
+          break;
+        default:   // CT_XU
+          ok = dag_wait(&cA[i * nbk + k], k + 1, fl, t0, limit_ns) &&
+               (j == k ? dag_wait(&cA[k * nbk + k], k + 1, fl, t0, limit_ns)
+                       : dag_wait(&cX[k * nbk + j], k - j + 1, fl, t0, limit_ns)) &&
+               dag_wait(&cX[i * nbk + j], k - j, fl, t0, limit_ns);
+          break;
+      }
+      if (ok) __threadfence();
+      s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;   // a timeout: every other task gives up at its next wait
+    float s[4], c[4];
+    if (kind == CT_F) {
+      // The critical chain, block step after block step in this CTA; X_{k-1,k-1} stays in S2.
+      bool ok = true;
+      for (int k = 0; k < nbk; ++k) {
+        if (k > 0) {
+          // the trailing updates of A_{k,k-1} and A_kk by steps 0 .. k-2 (other CTAs)
+          if (tid == 0) {
+            const uint64_t t0 = global_ns();
+            const bool w = dag_wait(&cA[k * nbk + k - 1], k - 1, fl, t0, limit_ns) &&
+                           dag_wait(&cA[k * nbk + k], k - 1, fl, t0, limit_ns);
+            if (w) __threadfence();
+            s_ok = w ? 1 : 0;
+          }
+          __syncthreads();
+          if (!s_ok) {
+            ok = false;
+            break;
+          }
+          // L_{k,k-1} = A_{k,k-1} X_{k-1,k-1}^T, published before the diagonal work
+          load_df_cg(S1, Ah, Al, tile(k, k - 1), mp);
+          __syncthreads();
+          df_tile_mul<false, true>(S1, S2, s, c);
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const size_t a = tile(k, k - 1) + (size_t)(e / kNB) * mp + e % kNB;
+            float h, l;
+            fast_two_sum(s[q], c[q], h, l);
+            Ah[a] = h;
+            Al[a] = l;
+            S1.h[e / kNB][e % kNB] = h;
+            S1.l[e / kNB][e % kNB] = l;
+          }
+          dag_publish(&cA[k * nbk + k - 1], k);
+          df_tile_mul<false, true>(S1, S1, s, c);   // L L^T
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const size_t a = tile(k, k) + (size_t)(e / kNB) * mp + e % kNB;
+            float h = __ldcg(Ah + a), l = __ldcg(Al + a);
+            df_add(h, l, -s[q], -c[q]);
+            S1.h[e / kNB][e % kNB] = h;
+            S1.l[e / kNB][e % kNB] = l;
+          }
+        } else {
+          load_df_cg(S1, Ah, Al, 0, mp);
+        }
+        if (tid < kNB) q0[tid] = Q0[(size_t)(k * kNB + tid) * mp + k * kNB + tid];
+        __syncthreads();
+        if (!diag_block(S1, Ah, Al, Xh, Xl, tile(k, k), mp, q0, S2) && tid == 0)
+          atomicExch(&fl[FL_BREAK], 1);
+        dag_publish(&cA[k * nbk + k], k + 1);
+      }
+      if (!ok) break;
+      continue;
+    }
+    float* dh;
+    float* dl;
+    size_t off;
+    bool acc;   // tile -= product, else tile = product
+    int* cnt;
+    int val;
+    switch (kind) {
+      case CT_T:   // L_ik = A_ik X_kk^T
+        off = tile(i, k);
+        load_df_cg(S1, Ah, Al, off, mp);
+        load_df_cg(S2, Xh, Xl, tile(k, k), mp);
+        __syncthreads();
+        df_tile_mul<false, true>(S1, S2, s, c);
+        dh = Ah, dl = Al, acc = false, cnt = &cA[i * nbk + k], val = k + 1;
+        break;
+      case CT_U:   // A_ij -= L_ik L_jk^T
+        off = tile(i, j);
+        load_df_cg(S1, Ah, Al, tile(i, k), mp);
+        load_df_cg(S2, Ah, Al, tile(j, k), mp);
+        __syncthreads();
+        df_tile_mul<false, true>(S1, S2, s, c);
+        dh = Ah, dl = Al, acc = true, cnt = &cA[i * nbk + j], val = k + 1;
+        break;
+      case CT_XS:   // X_kj <- X_kk X_kj
+        off = tile(k, j);
+        load_df_cg(S1, Xh, Xl, tile(k, k), mp);
+        load_df_cg(S2, Xh, Xl, off, mp);
+        __syncthreads();
+        df_tile_mul<false, false>(S1, S2, s, c);
+        dh = Xh, dl = Xl, acc = false, cnt = &cX[k * nbk + j], val = k - j + 1;
+        break;
+      default:   // CT_XU: X_ij -= L_ik X_kj
+        off = tile(i, j);
+        load_df_cg(S1, Ah, Al, tile(i, k), mp);
+        load_df_cg(S2, Xh, Xl, tile(k, j), mp);
+        __syncthreads();
+        df_tile_mul<false, false>(S1, S2, s, c);
+        dh = Xh, dl = Xl, acc = true, cnt = &cX[i * nbk + j], val = k - j + 1;
+        break;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      const size_t a = off + (size_t)(e / kNB) * mp + e % kNB;
+      float h, l;
+      if (acc) {
+        h = __ldcg(dh + a);
+        l = __ldcg(dl + a);
+        df_add(h, l, -s[q], -c[q]);
+      } else {
+        fast_two_sum(s[q], c[q], h, l);
+      }
+      dh[a] = h;
+      dl[a] = l;
+    }
+    dag_publish(cnt, val);
+  }
+}
+
+// Task list of the one-launch sweep for nbk blocks (order above); returns the count, writes
+// the codes to out when out is not null.
+size_t chol_dag_tasks(int nbk, uint32_t* out) {
+  size_t n = 0;
+  auto put = [&](uint32_t kind, int i, int j, int k) {
+    if (out) out[n] = ct_pack(kind, i, j, k);
+    ++n;
+  };
+  auto step = [&](int k) {
+    for (int i = k + 2; i < nbk; ++i) put(CT_T, i, k, k);
+    for (int j = 0; j < k; ++j) put(CT_XS, k, j, k);
+    const bool ahead = k + 2 < nbk;   // the two tiles F(k + 2) reads
+    if (ahead) {
+      put(CT_U, k + 2, k + 1, k);
+      put(CT_U, k + 2, k + 2, k);
+    }
+    for (int j = k + 1; j < nbk; ++j)
+      for (int i = j; i < nbk; ++i) {
+        if (i == k + 1 && j == k + 1) continue;
+        if (ahead && i == k + 2 && (j == k + 1 || j == k + 2)) continue;
+        put(CT_U, i, j, k);
+      }
+    for (int i = k + 1; i < nbk; ++i)
+      for (int j = 0; j <= k; ++j) put(CT_XU, i, j, k);
+  };
+  put(CT_F, 0, 0, 0);
+  for (int k = 0; k < nbk; ++k) step(k);
+  return n;
+}
+
 // M = X^T X (lower tiles, summed over block rows q >= i) stored as DF pairs (Mh, Ml), mirrored.
 __global__ void __launch_bounds__(256) k_ch_xtx(const float* Xh, const float* Xl, float* Mh,
                                                 float* Ml, int mp, int nbk, const int* fl) {
@@ -694,6 +981,26 @@ cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, 
     const int nupd = r * (r + 1) / 2 + r * (kb + 1);
     if (nupd > 0) { note_launch(); k_ch_update<<<nupd, 256, 0, st>>>(Ah, Al, Xh, Xl, Q0, mp, nbk, kb, fl); }
   }
+  if (form_m) { note_launch(); k_ch_xtx<<<nbk * (nbk + 1) / 2, 256, 0, st>>>(Xh, Xl, Ah, Al, mp, nbk, fl); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_dag(double* M, double* X, const double* Q0, int mp, int m, double eps,
+                            const uint32_t* tasks, int ntasks, int* sync, int num_sms, int* fl,
+                            cudaStream_t st, bool form_m) {
+  const int nbk = mp / kNB;
+  const size_t mm = (size_t)mp * mp;
+  float* Ah = reinterpret_cast<float*>(M);
+  float* Al = Ah + mm;
+  float* Xh = reinterpret_cast<float*>(X);
+  float* Xl = Xh + mm;
+  cudaError_t e = cudaMemsetAsync(X, 0, mm * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(sync, 0, chol_dag_sync_words(nbk) * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  { note_launch(); k_q_to_df<<<1024, 256, 0, st>>>(Q0, mp, m, eps, Ah, Al); }
+  const int grid = std::max(1, std::min(ntasks, num_sms * kDagCtasPerSm));
+  { note_launch(); k_ch_dag<<<grid, 256, 0, st>>>(Ah, Al, Xh, Xl, Q0, mp, nbk, tasks, ntasks, sync, fl, kWaitLimitNs); }
   if (form_m) { note_launch(); k_ch_xtx<<<nbk * (nbk + 1) / 2, 256, 0, st>>>(Xh, Xl, Ah, Al, mp, nbk, fl); }
   return cudaGetLastError();
 }

@@ -91,6 +91,7 @@ lp_status lp_params_default(lp_params* p) {
   p->autotune = 1;
   p->shared_cg = 0;
   p->persistent_cg = 0;
+  p->factor_dag = 1;
   return LP_OK;
 }
 
@@ -199,7 +200,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->colptr);
   dfree(c->rowidx);
   dfree(c->vals);
-  void* bufs[] = {c->pbar, c->Mf64, c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
+  void* bufs[] = {c->chtasks, c->chsync, c->pbar, c->Mf64, c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
@@ -366,7 +367,7 @@ static lp_status sync_scalars(lp_ctx* c) {
   LP_CU(cudaStreamSynchronize(c->st));
   if (!c->ev_pending.empty()) prof_harvest(c);
   if (c->fl_h[FL_TIMEOUT])
-    return fail(LP_ERR_TIMEOUT, "a bounded wait for a bulk copy of A gave up");
+    return fail(LP_ERR_TIMEOUT, "a bounded wait in a kernel gave up (a bulk copy or a task it depends on)");
   return LP_OK;
 }
 
@@ -911,9 +912,33 @@ static lp_status form_m_tensor_cores(lp_ctx* c) {
 
 // Cholesky factor and inverse of (Q + eps diag Q) with M = X^T X (form_m) on the tensor cores
 // when the buffers allow, else in the factor's own double-float kernel.
+// Task list and counters of the one-launch Cholesky sweep, built on first use (they depend on
+// mp only).  False when the sweep keeps the block-step launches.
+static lp_status ensure_dag(lp_ctx* c, bool* use) {
+  const int nbk = c->mp / kNB;
+  *use = c->prm.factor_dag != 0 && nbk <= kDagMaxBlocks;
+  if (!*use || c->chtasks) return LP_OK;
+  std::vector<uint32_t> t(chol_dag_tasks(nbk, nullptr));
+  chol_dag_tasks(nbk, t.data());
+  AllocStream as(c->st);
+  LP_TRY(dalloc(&c->chtasks, t.size()));
+  LP_TRY(dalloc(&c->chsync, chol_dag_sync_words(nbk)));
+  LP_CU(cudaMemcpyAsync(c->chtasks, t.data(), t.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                        c->st));
+  LP_CU(cudaStreamSynchronize(c->st));
+  c->chntasks = (int)t.size();
+  return LP_OK;
+}
+
 static lp_status chol_inverse(lp_ctx* c, double eps, bool form_m) {
   const bool tc = form_m && xtx_on_tensor_cores(c);
-  LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps, c->fl, c->st, form_m && !tc));
+  bool dag = false;
+  LP_TRY(ensure_dag(c, &dag));
+  if (dag)
+    LP_CU(launch_chol_dag(c->M, c->X, c->Q, c->mp, c->m, eps, c->chtasks, c->chntasks, c->chsync,
+                          c->num_sms, c->fl, c->st, form_m && !tc));
+  else
+    LP_CU(launch_chol_inverse(c->M, c->X, c->Q, c->mp, c->m, eps, c->fl, c->st, form_m && !tc));
   if (tc) LP_TRY(form_m_tensor_cores(c));
   return LP_OK;
 }
@@ -1843,6 +1868,8 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
   b += (double)gram_tc_digit_bytes(m, w) + 4.0 * gram_tc_rows(m) +
        (double)gram_tc_part_bytes(m, mp, w, num_sms);                      // tensor-core Gram
   b += 3.0 * mp * mp * 8 + (double)round_up(m, 2) * w * 8;               // second factor stage
+  if (p.factor_dag && mp / kNB <= kDagMaxBlocks)                           // one-launch sweep
+    b += 4.0 * (double)chol_dag_tasks(mp / kNB, nullptr) + 4.0 * chol_dag_sync_words(mp / kNB);
   b += (SC_COUNT + kMaxRedBlocks * 8) * 8.0 + FL_COUNT * 4 + 64;
   b += 8 * dm + 8 * dn;                                                    // b, c
   if (layout != LP_CSR) {

@@ -209,6 +209,9 @@ struct lp_ctx {
   long long graph_launches = 0;
   long long persistent_launches = 0;
   unsigned* pbar = nullptr;     // grid barrier words of the persistent CG loop (32)
+  uint32_t* chtasks = nullptr;  // task list of the one-launch Cholesky sweep (allocated on first use)
+  int chntasks = 0;
+  int* chsync = nullptr;        // its claim counter and tile counters
 
   // profiling (CUDA events on st)
   struct EvPair {
@@ -405,6 +408,15 @@ cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double
 // form_m = false skips M = X^T X (the caller forms it, or needs only X).
 cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
                                 int* fl, cudaStream_t st, bool form_m = true);
+// The same Cholesky sweep as one launch of tile tasks in dependency order (k_factor.cu):
+// tasks from chol_dag_tasks (4 bytes each), sync = chol_dag_sync_words zeroed-per-launch words.
+constexpr int kDagCtasPerSm = 2;    // CTAs per SM claiming tasks (126 registers a thread: 2 fit)
+constexpr int kDagMaxBlocks = 256;  // nbk above this keeps the block-step launches
+inline size_t chol_dag_sync_words(int nbk) { return 2 + 2 * (size_t)nbk * nbk; }
+size_t chol_dag_tasks(int nbk, uint32_t* out);
+cudaError_t launch_chol_dag(double* M, double* X, const double* Q0, int mp, int m, double eps,
+                            const uint32_t* tasks, int ntasks, int* sync, int num_sms, int* fl,
+                            cudaStream_t st, bool form_m = true);
 cudaError_t launch_df_to_double(const double* Mdf, int mp, int m, double* out, int ld,
                                 cudaStream_t st);
 cudaError_t launch_symv_f64(const double* M, int mp, int m, const double* r, double* z,

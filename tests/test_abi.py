@@ -53,7 +53,7 @@ def test_params_default_and_status_strings(lib):
     assert p.tol == 1e-8 and p.sigma == 0.5 and p.sketch_s == 4 and p.cg_rel_tol == 1e-6
     assert ctypes.sizeof(pkg.lp_params) == 104
     assert p.use_graphs == 1 and p.gram_tensor_cores == 1 and p.autotune == 1
-    assert p.shared_cg == 0 and p.persistent_cg == 0
+    assert p.shared_cg == 0 and p.persistent_cg == 0 and p.factor_dag == 1
     from paper_2003_08072_gb300 import _binding
 
     assert _binding.status_str(0) == "LP_OK"

@@ -14,7 +14,7 @@ STRUCTS = {
     "lp_params": ["tol", "cg_rel_tol", "sigma", "gamma", "cg_max_iter", "ipm_max_iter",
                   "refine_max", "sketch_s", "sketch_w", "cg_theory_rule", "seed", "stream_dtype",
                   "cg_batch", "inner_solver", "sketch_kind", "use_graphs",
-                  "gram_tensor_cores", "autotune", "shared_cg", "persistent_cg"],
+                  "gram_tensor_cores", "autotune", "shared_cg", "persistent_cg", "factor_dag"],
     "lp_info": ["ipm_iters", "cg_iters_total", "cg_iters_last", "refine_steps", "rp_rel",
                 "rd_rel", "gap_rel", "mu", "obj", "alpha_max", "alpha", "f_norm", "v_norm",
                 "status", "f_target", "stream_dtype", "stream_switch_iter", "factor_two_stage",

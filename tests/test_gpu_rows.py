@@ -165,6 +165,41 @@ def test_factor_flags_rank_deficient_sketch():
     assert e.value.status == pkg._binding.LP_ERR_BREAKDOWN
 
 
+@pytest.mark.parametrize("m", [40, 300, 1000, 2100])
+def test_factor_one_launch_sweep_equals_block_steps(m):
+    """The Cholesky sweep as one launch of tile tasks claimed in dependency order gives bitwise
+    the factor of the two-launches-per-block-step sweep (each tile sees the same operations in
+    the same order), on a sketch with kappa(Q) ~ 1e10; both match the inverse of G G^T.  The
+    sizes give 2, 10, 32 and 66 diagonal blocks of 32."""
+    w = 4 * m
+    rng = np.random.default_rng(m)
+    G = rng.standard_normal((m, w)) * np.logspace(0, -5, m)[:, None]
+    out = {}
+    for dag in (0, 1):
+        solver, A, lp, prm = make("dense", m, 2 * m, "f64", factor_dag=dag)
+        Q, Mi = solver.factor(T(np.ascontiguousarray(G.T)))
+        out[dag] = (N(Q), N(Mi))
+        del solver
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    OQ = G @ G.T
+    kappa = np.linalg.cond(OQ)
+    assert kappa > 1e9
+    assert close(out[1][1], np.linalg.inv(OQ), 1e-15 * kappa * m)
+
+
+def test_factor_one_launch_sweep_flags_rank_deficient_sketch():
+    import paper_2003_08072_gb300 as pkg
+
+    for dag in (0, 1):
+        solver, A, lp, prm = make("dense", 300, 2000, "f64", factor_dag=dag)
+        G = np.random.default_rng(1).standard_normal((300, 1200))
+        G[250] = G[17]                  # rank(G) = 299: a pivot of the 8th block is lost
+        with pytest.raises(pkg.LPError) as e:
+            solver.factor(T(np.ascontiguousarray(G.T)))
+        assert e.value.status == pkg._binding.LP_ERR_BREAKDOWN
+
+
 # ------------------------------------------------------------------ a4: A D^2 A^T v
 
 @pytest.mark.parametrize("case", CASES)
