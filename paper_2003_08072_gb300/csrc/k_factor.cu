@@ -700,7 +700,7 @@ __device__ __forceinline__ void dag_publish(int* cnt, int v) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_ch_dag(float* Ah, float* Al, float* Xh, float* Xl,
+__global__ void __launch_bounds__(256, 1) k_ch_dag(float* Ah, float* Al, float* Xh, float* Xl,
                                                 const double* __restrict__ Q0, int mp, int nbk,
                                                 const uint32_t* __restrict__ tasks, int ntasks,
                                                 int* sync, int* fl, uint64_t limit_ns) {
