@@ -88,8 +88,10 @@ typedef struct {
                             LP_ERR_NOT_CONVERGED (0) */
   int32_t sketch_kind;   /* LP_SKETCH_SPARSE (0): sketch_s nonzeros +-1/sqrt(s) per row of W (Sec. 2);
                             LP_SKETCH_GAUSSIAN (1): W with N(0, 1/w) entries (Sec. 5, the sketch of the
-                            experiments, Sec. 6), dense A only; forming A D W costs 2 m n w, meant for
-                            the small LPs of the experiments (0) */
+                            experiments, Sec. 6), dense A only: entry (i, b) is q_j / (2^8 sqrt(w)),
+                            q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14)) for the cell j = h >> 50 of the
+                            hash h = SplitMix64(key_k ^ (i w + b)) (normal quantiles on a 2^-8 grid);
+                            forming A D W costs 2 m n w (tensor cores: gram_tensor_cores) (0) */
   int32_t use_graphs;    /* 1: after a context's first CG solve, each CG solve runs as one CUDA graph
                             launch whose WHILE node repeats the CG iteration on the device until the
                             stop rule holds (no host round trip per cg_batch); 0: every CG iteration
@@ -98,8 +100,10 @@ typedef struct {
   int32_t gram_tensor_cores; /* 1: the Gram product Q = (A D W)(A D W)^T of the factor runs on the tensor
                             cores (tcgen05), made exact by splitting each row of the sketch into nine
                             BF16 digit slices of 6 bits (each entry accurate to ~2^-52 sqrt(w)
-                            |G_i| |G_j|, finer than the double-float product); 0: double-float product
-                            on the FP32 pipes (1) */
+                            |G_i| |G_j|, finer than the double-float product), and so does the
+                            Gaussian sketch A D W (rows of A D in nine digit slices, W's grid values
+                            in two; extra device memory ~(18 m + 4 w) n bytes); 0: double-float
+                            products on the FP32 pipes (1) */
   int32_t autotune;      /* 1: lp_create times the CG product's launch shapes (group width, pipeline
                             stages, CTAs per SM) on the matrix itself (A of 64 MB and more; a few ms,
                             kept per shape for the process) and keeps the fastest; 0: fixed rule (1) */

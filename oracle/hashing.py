@@ -25,10 +25,15 @@ distinct, as in OSNAP; with s = 1 this is CountSketch.  W is redrawn each IPM
 iteration (Algorithm 2, step (a)) by changing k, and the same W serves the
 preconditioner and the correction vector of that iteration (Sec. 4, after
 Lemma 4.1).
+
+The Gaussian W (Sec. 5, and the sketch of the experiments, Sec. 6) is drawn from the same key
+by inverting the normal CDF on 2^14 equiprobable cells, its values rounded to a grid of 2^-8
+(``gaussian_W``), so that both sides produce it exactly.
 """
 from __future__ import annotations
 
 import numpy as np
+from scipy import special
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -75,16 +80,28 @@ def sketch_indices(seed: int, k: int, n: int, s: int, w: int):
     return bucket, sign
 
 
+GAUSS_BITS = 14   # the Gaussian W draws from 2^14 equiprobable quantile cells
+
+
+def gaussian_grid() -> np.ndarray:
+    """Values of the Gaussian sketch's entries times sqrt(w) 2^8: for cell j of 2^14 equally
+    likely cells, q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14)) (Phi the standard normal CDF, by
+    scipy's ndtri), an integer with |q_j| <= 1026."""
+    j = np.arange(2**GAUSS_BITS, dtype=np.float64)
+    return np.rint(256.0 * special.ndtri((j + 0.5) * 2.0**-GAUSS_BITS))
+
+
 def gaussian_W(seed: int, k: int, n: int, w: int, rows=None) -> np.ndarray:
     """Dense Gaussian sketching matrix W (n x w) of iteration k, entries ~ N(0, 1/w).
 
     The Gaussian sketch of the paper's experiments (Sec. 6) and of Sec. 5, generated from the
-    same per-iteration key: for entry (i, b), with t = i*w + b,
-        h1 = splitmix64(key_k ^ 2t),  h2 = splitmix64(key_k ^ (2t + 1)),
-        u1 = ((h1 >> 40) + 1) 2^-24 in (0, 1],  u2 = (h2 >> 40) 2^-24 in [0, 1),
-        z  = sqrt(-2 ln u1) cos(2 pi u2)      (Box & Muller, Ann. Math. Stat. 1958),
-        W[i, b] = z / sqrt(w).
-    24-bit uniforms are exact in FP32, so both sides start from identical u1, u2.
+    same per-iteration key by inversion of the normal CDF: for entry (i, b), with t = i*w + b,
+        h = splitmix64(key_k ^ t),  j = h >> 50  (one of 2^14 equiprobable cells),
+        W[i, b] = q_j / (2^8 sqrt(w)),  q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14)).
+    The entries are N(0, 1) quantiles on a grid of 2^-8 (the distribution's mass per cell is
+    2^-14, its tails cut at 4.0 sigma), scaled by 1/sqrt(w); being integers over 2^8 sqrt(w),
+    they are the same on every side that evaluates them, and the sketch A D W can be formed
+    exactly from a fixed-point split of A D.
     ``rows`` restricts the output to those row indices (default: all n).
     """
     key = iteration_key(seed, k)
@@ -92,9 +109,6 @@ def gaussian_W(seed: int, k: int, n: int, w: int, rows=None) -> np.ndarray:
     b = np.arange(w, dtype=np.uint64)[None, :]
     with np.errstate(over="ignore"):
         t = i * np.uint64(w) + b
-        h1 = splitmix64(key ^ (np.uint64(2) * t))
-        h2 = splitmix64(key ^ (np.uint64(2) * t + np.uint64(1)))
-    u1 = ((h1 >> np.uint64(40)).astype(np.float64) + 1.0) * 2.0**-24
-    u2 = (h2 >> np.uint64(40)).astype(np.float64) * 2.0**-24
-    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
-    return z / np.sqrt(w)
+        h = splitmix64(key ^ t)
+    cell = (h >> np.uint64(64 - GAUSS_BITS)).astype(np.int64)
+    return gaussian_grid()[cell] / (256.0 * np.sqrt(w))

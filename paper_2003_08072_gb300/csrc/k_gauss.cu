@@ -1,19 +1,23 @@
 // Gaussian sketch A D W (Sec. 5; the sketch of the paper's experiments, Sec. 6) and W u.
 //
-// W (n x w) has entries N(0, 1/w), generated on the fly from the iteration key of the sparse
-// sketch: for entry (i, b), t = i w + b,
-//   h1 = SplitMix64(key ^ 2t),  h2 = SplitMix64(key ^ (2t + 1)),
-//   u1 = ((h1 >> 40) + 1) 2^-24,  u2 = (h2 >> 40) 2^-24   (exact in FP32),
-//   W[i, b] = sqrt(-2 ln u1) cos(2 pi u2) / sqrt(w)        (Box & Muller 1958).
-// Every use of W (the sketch and W u) evaluates the same device function, so the sketch and
-// the correction vector see the same W and A S^-1 v = (A D W) u holds to the accuracy of G.
+// W (n x w) has entries N(0, 1/w), drawn by inversion of the normal CDF from the iteration key
+// of the sparse sketch: for entry (i, b), t = i w + b,
+//   h = SplitMix64(key ^ t),  j = h >> 50  (one of 2^14 equiprobable cells),
+//   W[i, b] = q_j / (2^8 sqrt(w)),  q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14)),
+// Phi the standard normal CDF.  The table q (|q_j| <= 1026) is computed once per process on the
+// host (gauss_grid) and kept in each context's device memory.  Every use of W (the sketch on
+// either path and W u) reads the same table, so the sketch and the correction vector see the
+// same W and A S^-1 v = (A D W) u holds to the accuracy of G; the integer grid is what lets
+// the tensor-core sketch (k_sketch_tc.cu) form A D W exactly.
 //
-// G = A D W is a dense product of cost 2 m n w, affordable for the small LPs of the paper's
-// experiments (m in the hundreds, w = 4m): a CTA owns 256 rows, 8 sketch columns and a slice of
+// This file's G = A D W is the product on the CUDA cores in double-float, of cost 2 m n w
+// (the tensor-core path is the default): a CTA owns 256 rows, 8 sketch columns and a slice of
 // the n columns of A (slices spread the work over the GPU when m and w are small), walks its
 // slice in chunks, generates the chunk's 8 columns of D W into shared memory as double-float
 // coefficients, accumulates in double-float and adds its partial sums into G with FP64
 // atomics; W u takes one thread per row of W with FP64 accumulation.
+#include <cmath>
+
 #include "dev_util.cuh"
 
 namespace lpk {
@@ -27,13 +31,11 @@ __device__ __forceinline__ uint64_t sm64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ float gauss_w(uint64_t key, int64_t i, int b, int w, float rsw) {
+// q of entry (i, b): W[i, b] = q / (2^8 sqrt(w))
+__device__ __forceinline__ int gauss_q(uint64_t key, int64_t i, int b, int w,
+                                       const int16_t* __restrict__ gq) {
   const uint64_t t = (uint64_t)i * (uint64_t)w + (uint64_t)b;
-  const uint64_t h1 = sm64(key ^ (2ull * t));
-  const uint64_t h2 = sm64(key ^ (2ull * t + 1ull));
-  const float u1 = (float)((h1 >> 40) + 1ull) * 0x1p-24f;
-  const float u2 = (float)(h2 >> 40) * 0x1p-24f;
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2) * rsw;
+  return __ldg(gq + (sm64(key ^ t) >> 50));
 }
 
 constexpr int kGB = 8;     // sketch columns per CTA
@@ -43,7 +45,8 @@ constexpr int kGC = 128;   // columns of A per chunk
 
 template <typename TA>
 __global__ void __launch_bounds__(256) k_sketch_gauss(const TA* __restrict__ A, int64_t lda, int m,
-                                                      int64_t n, int w, uint64_t key, float rsw,
+                                                      int64_t n, int w, uint64_t key, double rsw,
+                                                      const int16_t* __restrict__ gq,
                                                       const double* __restrict__ d,
                                                       double* __restrict__ G, int ldg,
                                                       int64_t slice) {
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(256) k_sketch_gauss(const TA* __restrict__ A, 
       const int ii = e / kGB, bb = e % kGB;
       const int64_t i = i0 + ii;
       double cf = 0.0;
-      if (i < iend && b0 + bb < w) cf = d[i] * (double)gauss_w(key, i, b0 + bb, w, rsw);
+      if (i < iend && b0 + bb < w) cf = d[i] * ((double)gauss_q(key, i, b0 + bb, w, gq) * rsw);
       split_double(cf, ch[ii][bb], cl[ii][bb]);
     }
     __syncthreads();
@@ -87,17 +90,41 @@ __global__ void __launch_bounds__(256) k_sketch_gauss(const TA* __restrict__ A, 
       if (b0 + q < w) atomicAdd(&G[(size_t)(b0 + q) * ldg + r], (double)s[q] + (double)c[q]);
 }
 
-__global__ void k_apply_W_gauss(uint64_t key, int64_t n, int w, float rsw,
-                                const double* __restrict__ u, double* __restrict__ wu) {
+__global__ void k_apply_W_gauss(uint64_t key, int64_t n, int w, double rsw,
+                                const int16_t* __restrict__ gq, const double* __restrict__ u,
+                                double* __restrict__ wu) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int b = 0; b < w; ++b) acc = fma((double)gauss_w(key, i, b, w, rsw), u[b], acc);
-    wu[i] = acc;
+    for (int b = 0; b < w; ++b) acc = fma((double)gauss_q(key, i, b, w, gq), u[b], acc);
+    wu[i] = acc * rsw;
   }
 }
 
-static uint64_t gauss_key(uint64_t seed, int k) {
+// q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14)): Phi^{-1} by bisection on Phi(z) = erfc(-z / sqrt 2)
+// / 2 over [-10, 0] to the resolution of FP64 (the cells below 1/2; the upper half by symmetry,
+// q_{N-1-j} = -q_j).  No table value lies within 1e-5 of a rounding tie, far above the error of
+// this evaluation, so any accurate evaluation of Phi^{-1} gives the same integers.
+void gauss_grid(int16_t* q) {
+  constexpr int N = 1 << kGaussBits;
+  for (int j = 0; j < N / 2; ++j) {
+    const double p = (j + 0.5) / N;
+    double lo = -10.0, hi = 0.0;
+    for (int it = 0; it < 80 && hi - lo > 0.0; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (0.5 * std::erfc(-mid * 0.70710678118654752440) < p)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const long v = std::lrint(256.0 * 0.5 * (lo + hi));
+    q[j] = (int16_t)v;
+    q[N - 1 - j] = (int16_t)(-v);
+  }
+}
+
+uint64_t gauss_iteration_key(uint64_t seed, int k) {
   auto h = [](uint64_t x) {
     uint64_t z = x + 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -108,10 +135,10 @@ static uint64_t gauss_key(uint64_t seed, int k) {
 }
 
 cudaError_t launch_sketch_gauss(lp_dtype ta, const void* A, int64_t lda, int m, int64_t n, int w,
-                                uint64_t seed, int k, const double* d, double* G, int ldg,
-                                cudaStream_t st) {
-  const uint64_t key = gauss_key(seed, k);
-  const float rsw = (float)(1.0 / sqrt((double)w));
+                                uint64_t seed, int k, const int16_t* gq, const double* d, double* G,
+                                int ldg, cudaStream_t st) {
+  const uint64_t key = gauss_iteration_key(seed, k);
+  const double rsw = 1.0 / (256.0 * sqrt((double)w));
   if (ta != LP_F32 && ta != LP_F64) return cudaErrorInvalidValue;
   // slices of the n columns so that about 4 CTAs per SM have work
   int dev = 0, sms = 152;
@@ -131,24 +158,24 @@ cudaError_t launch_sketch_gauss(lp_dtype ta, const void* A, int64_t lda, int m, 
   dim3 grid((unsigned)((w + kGB - 1) / kGB), (unsigned)((m + 255) / 256), (unsigned)nsl);
   if (ta == LP_F32) {
     note_launch();
-    k_sketch_gauss<float><<<grid, 256, 0, st>>>((const float*)A, lda, m, n, w, key, rsw, d, G, ldg,
-                                                 slice);
+    k_sketch_gauss<float><<<grid, 256, 0, st>>>((const float*)A, lda, m, n, w, key, rsw, gq, d, G,
+                                                 ldg, slice);
   } else {
     note_launch();
-    k_sketch_gauss<double><<<grid, 256, 0, st>>>((const double*)A, lda, m, n, w, key, rsw, d, G,
-                                                  ldg, slice);
+    k_sketch_gauss<double><<<grid, 256, 0, st>>>((const double*)A, lda, m, n, w, key, rsw, gq, d,
+                                                  G, ldg, slice);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_W_gauss(uint64_t seed, int k, int64_t n, int w, const double* u, double* wu,
-                                 cudaStream_t st) {
+cudaError_t launch_apply_W_gauss(uint64_t seed, int k, int64_t n, int w, const int16_t* gq,
+                                 const double* u, double* wu, cudaStream_t st) {
   int64_t g = (n + 255) / 256;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
   note_launch();
-  k_apply_W_gauss<<<(unsigned)g, 256, 0, st>>>(gauss_key(seed, k), n, w,
-                                               (float)(1.0 / sqrt((double)w)), u, wu);
+  k_apply_W_gauss<<<(unsigned)g, 256, 0, st>>>(gauss_iteration_key(seed, k), n, w,
+                                               1.0 / (256.0 * sqrt((double)w)), gq, u, wu);
   return cudaGetLastError();
 }
 

@@ -200,7 +200,7 @@ extern "C" void lp_destroy(lp_ctx* c) {
   dfree(c->colptr);
   dfree(c->rowidx);
   dfree(c->vals);
-  void* bufs[] = {c->chtasks, c->chsync, c->pbar, c->Mf64, c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
+  void* bufs[] = {c->gq, c->gtc, c->chtasks, c->chsync, c->pbar, c->Mf64, c->dfc, c->d2f, c->b, c->c, c->x, c->y, c->s, c->d2, c->d, c->rd, c->t, c->wu, c->dx, c->ds,
                   c->rp, c->p, c->dy, c->r, c->z, c->dd, c->q, c->rtil, c->qhat, c->res, c->tm,
                   c->dyacc, c->rhs, c->r_alt, c->d_alt, c->part, c->hb, c->cnt, c->start, c->cursor, c->list, c->coef, c->qf, c->G, c->Gdf,
                   c->u, c->Q, c->M, c->X, c->Qsplit, c->sc, c->fl, c->bpart,
@@ -264,6 +264,14 @@ static lp_status alloc_workspace(lp_ctx* c) {
   LP_TRY(dalloc((unsigned char**)&c->gdig, gram_tc_digit_bytes(m, c->w)));
   LP_TRY(dalloc(&c->gex, (size_t)gram_tc_rows(m)));
   LP_TRY(dalloc((unsigned char**)&c->gpart, gram_tc_part_bytes(m, c->mp, c->w, c->num_sms)));
+  // quantile table of the Gaussian W (the sketch needs a dense A)
+  if (!c->sparse) {
+    static std::once_flag once;
+    static int16_t table[1 << kGaussBits];
+    std::call_once(once, [] { gauss_grid(table); });
+    LP_TRY(dalloc(&c->gq, (size_t)1 << kGaussBits));
+    LP_CU(cudaMemcpyAsync(c->gq, table, sizeof(table), cudaMemcpyHostToDevice, c->st));
+  }
   // scalars
   LP_TRY(dalloc(&c->pbar, 32));
   LP_TRY(dalloc(&c->sc, SC_COUNT));
@@ -856,8 +864,23 @@ static lp_status run_residuals(lp_ctx* c, const double* x, const double* y, cons
 static lp_status run_sketch(lp_ctx* c, const double* d, int k, double* G) {
   PhaseScope ps(c, LP_PH_SKETCH);
   if (c->prm.sketch_kind == LP_SKETCH_GAUSSIAN) {
-    LP_CU(launch_sketch_gauss(c->a_dtype, c->A, c->lda, c->m, c->n, c->w, c->prm.seed, k, d, G,
-                              c->ldg, c->st));
+    if (c->prm.gram_tensor_cores) {
+      const size_t need = sketch_tc_work_bytes(c->m, c->n, c->w, c->num_sms);
+      if (c->gtc_bytes < need) {
+        AllocStream as(c->st);
+        dfree(c->gtc);
+        c->gtc = nullptr;
+        c->gtc_bytes = 0;
+        LP_TRY(dalloc((unsigned char**)&c->gtc, need));
+        c->gtc_bytes = need;
+      }
+      LP_CU(launch_sketch_tc(c->a_dtype, c->A, c->lda, c->m, c->n, c->w,
+                             gauss_iteration_key(c->prm.seed, k), d, c->gq, G, c->ldg, c->gtc,
+                             c->num_sms, c->fl, c->st));
+    } else {
+      LP_CU(launch_sketch_gauss(c->a_dtype, c->A, c->lda, c->m, c->n, c->w, c->prm.seed, k, c->gq,
+                                d, G, c->ldg, c->st));
+    }
     return LP_OK;
   }
   LP_CU(cudaMemsetAsync(c->cnt, 0, (c->w + 1) * sizeof(int32_t), c->st));
@@ -1647,7 +1670,7 @@ static lp_status ipm_run(lp_ctx* c, double* x, double* y, double* s, bool start_
     const double* wu_given = nullptr;
     if (c->prm.sketch_kind == LP_SKETCH_GAUSSIAN) {
       // the fused update gathers W u from the sparse W's buckets; the Gaussian W needs W u first
-      LP_CU(launch_apply_W_gauss(c->prm.seed, k, c->n, c->w, c->u, c->wu, c->st));
+      LP_CU(launch_apply_W_gauss(c->prm.seed, k, c->n, c->w, c->gq, c->u, c->wu, c->st));
       wu_given = c->wu;
     }
     st = run_step(c, c->x, c->y, c->s, c->rd, c->dyacc, c->t, wu_given, eta, mu0, c->dx, c->ds);
@@ -1730,7 +1753,7 @@ extern "C" lp_status lp_normal_solve(lp_ctx* c, const double* x, const double* s
   if (u) LP_CU(cudaMemcpyAsync(u, c->u, c->w * sizeof(double), cudaMemcpyDefault, c->st));
   if (Atdy) LP_CU(cudaMemcpyAsync(Atdy, c->t, c->n * sizeof(double), cudaMemcpyDefault, c->st));
   if (Wu && c->prm.sketch_kind == LP_SKETCH_GAUSSIAN)
-    LP_CU(launch_apply_W_gauss(c->prm.seed, k, c->n, c->w, c->u, Wu, c->st));
+    LP_CU(launch_apply_W_gauss(c->prm.seed, k, c->n, c->w, c->gq, c->u, Wu, c->st));
   else if (Wu)
     LP_CU(launch_apply_W(c->hb, c->ss, c->u, c->n, Wu, c->st));
   LP_CU(cudaStreamSynchronize(c->st));
@@ -1872,6 +1895,9 @@ extern "C" uint64_t lp_footprint_bytes(int32_t m, int64_t n, lp_layout layout, l
     b += 4.0 * (double)chol_dag_tasks(mp / kNB, nullptr) + 4.0 * chol_dag_sync_words(mp / kNB);
   b += (SC_COUNT + kMaxRedBlocks * 8) * 8.0 + FL_COUNT * 4 + 64;
   b += 8 * dm + 8 * dn;                                                    // b, c
+  if (layout != LP_CSR) b += 2.0 * (1 << kGaussBits);                      // Gaussian W table
+  if (layout != LP_CSR && p.sketch_kind == LP_SKETCH_GAUSSIAN && p.gram_tensor_cores)
+    b += (double)sketch_tc_work_bytes(m, n, w, num_sms);                   // tensor-core sketch
   if (layout != LP_CSR) {
     const int lda = round_up(m, (int)(16 / dtype_size(a_dtype)));
     b += (double)lda * dn * es;

@@ -209,6 +209,9 @@ struct lp_ctx {
   long long graph_launches = 0;
   long long persistent_launches = 0;
   unsigned* pbar = nullptr;     // grid barrier words of the persistent CG loop (32)
+  int16_t* gq = nullptr;        // quantile table of the Gaussian W (dense A)
+  void* gtc = nullptr;          // digits and partial tiles of the tensor-core Gaussian sketch
+  size_t gtc_bytes = 0;
   uint32_t* chtasks = nullptr;  // task list of the one-launch Cholesky sweep (allocated on first use)
   int chntasks = 0;
   int* chsync = nullptr;        // its claim counter and tile counters
@@ -551,12 +554,21 @@ int gram_split_cap(int m, int w, int num_sms);
 // conversions
 cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, int m, int64_t n,
                                  void* dst, lp_dtype ddt, int ldd, cudaStream_t st);
-// Gaussian sketch G = A D W (dense A, FP32 or FP64) and W u, W from (seed, k) (k_gauss.cu)
+// Gaussian sketch G = A D W (dense A, FP32 or FP64) and W u, W from (seed, k) and the quantile
+// table gq of 2^kGaussBits entries (k_gauss.cu: CUDA cores; k_sketch_tc.cu: tensor cores)
+constexpr int kGaussBits = 14;
+void gauss_grid(int16_t* q);   // host: the table, q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14))
+uint64_t gauss_iteration_key(uint64_t seed, int k);
 cudaError_t launch_sketch_gauss(lp_dtype ta, const void* A, int64_t lda, int m, int64_t n, int w,
-                                uint64_t seed, int k, const double* d, double* G, int ldg,
-                                cudaStream_t st);
-cudaError_t launch_apply_W_gauss(uint64_t seed, int k, int64_t n, int w, const double* u, double* wu,
-                                 cudaStream_t st);
+                                uint64_t seed, int k, const int16_t* gq, const double* d, double* G,
+                                int ldg, cudaStream_t st);
+cudaError_t launch_apply_W_gauss(uint64_t seed, int k, int64_t n, int w, const int16_t* gq,
+                                 const double* u, double* wu, cudaStream_t st);
+// work: sketch_tc_work_bytes(m, n, w, num_sms) bytes of device memory, 256-byte aligned
+size_t sketch_tc_work_bytes(int m, int64_t n, int w, int num_sms);
+cudaError_t launch_sketch_tc(lp_dtype ta, const void* A, int64_t lda, int m, int64_t n, int w,
+                             uint64_t key, const double* d, const int16_t* gq, double* G, int ldg,
+                             void* work, int num_sms, int* fl, cudaStream_t st);
 int occupancy_cached(const void* func, int threads, size_t smem);
 // Raises (never lowers) a kernel's dynamic shared-memory limit to at least `bytes`.
 cudaError_t ensure_dyn_smem(const void* func, size_t bytes);

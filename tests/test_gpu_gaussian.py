@@ -1,7 +1,8 @@
 """Gaussian sketch (Sec. 5; the sketch of the paper's experiments, Sec. 6) on the GPU against
-the oracle.  Both sides generate W from the same counter (SplitMix64 uniforms, Box-Muller);
-the GPU evaluates the transcendentals in FP32, so W agrees to ~1e-7 relative and the
-products built from it to the same order."""
+the oracle.  Both sides draw W from the same counter and the normal quantile table on a 2^-8
+grid, computed independently (the oracle with scipy's ndtri, the library on the host by
+bisection on erfc); the entries are integers over 2^8 sqrt(w), identical on both sides, so
+the sketch agrees to the accuracy of the products."""
 import numpy as np
 import pytest
 
@@ -21,28 +22,60 @@ def N(t):
     return t.detach().cpu().numpy()
 
 
-def make(lp, dt=np.float64):
+def make(lp, dt=np.float64, At=None, **prm_kw):
     import paper_2003_08072_gb300 as pkg
 
     prm = pkg.lp_params_default()
     prm.sketch_kind = pkg._binding.LP_SKETCH_GAUSSIAN
-    At = lp.At.astype(dt)
+    for k, v in prm_kw.items():
+        setattr(prm, k, v)
+    At = (lp.At if At is None else At).astype(dt)
     return pkg.LPSolver.dense(T(At), T(lp.b), T(lp.c), params=prm), prm
 
 
-def test_gaussian_sketch_matches_oracle():
-    m, n = 40, 2000
-    lp = synth.dense_lp(0, m, n)
-    solver, prm = make(lp)
+@pytest.mark.parametrize("tc", [1, 0])
+@pytest.mark.parametrize("m,n,dt", [(40, 2000, np.float64), (130, 9001, np.float32),
+                                    (97, 12289, np.float64)])
+def test_gaussian_sketch_matches_oracle(tc, m, n, dt):
+    """G = A D W on the tensor cores (exact split, tc = 1) and on the CUDA cores (double-float,
+    tc = 0) against the oracle's FP64 product with the same W (integer grid values, identical
+    on both sides).  The shapes cross the 4096-column chunks of the tensor-core product with a
+    ragged last chunk and k block, and leave ragged tiles in m (32) and w = 4m (128); with
+    n w >= 4e6 entries every cell of the quantile table is drawn."""
+    lp = synth.dense_lp(0, m, n, dtype=dt)
+    solver, prm = make(lp, dt, gram_tensor_cores=tc)
     x, y, s = synth.iterate_point(3, m, n, spread=3.0)
     d = np.sqrt(x / s)
     k = 5
     G = N(solver.sketch(T(d), k))
     W = hashing.gaussian_W(prm.seed, k, n, 4 * m)
-    ref = lp.A @ (d[:, None] * W)
-    scale = np.abs(np.abs(lp.A) @ (d[:, None] * np.abs(W))).max()
-    assert np.abs(G - ref).max() <= 1e-6 * scale
+    A = lp.A.astype(np.float64)
+    ref = A @ (d[:, None] * W)
+    scale = np.abs(np.abs(A) @ (d[:, None] * np.abs(W))).max()
+    assert np.abs(G - ref).max() <= 1e-13 * scale
     solver.close()
+
+
+@pytest.mark.parametrize("tc,tol", [(1, 1e-13), (0, 1e-12)])
+def test_gaussian_sketch_entrywise(tc, tol):
+    """Every entry of G, relative to its own scale (|A| D |W|)_ic, including a row of A D nine
+    orders of magnitude below the others (its own exponent in the tensor-core split).  The
+    tensor-core product is exact up to the 2^-54 digit truncation of each row of A D; the
+    double-float sum on the CUDA cores accumulates n rounding errors of 2^-48."""
+    m, n = 70, 6000
+    lp = synth.dense_lp(2, m, n)
+    x, y, s = synth.iterate_point(7, m, n, spread=6.0)
+    d = np.sqrt(x / s)
+    At = lp.At.copy()
+    At[:, 11] *= 1e-9
+    solver, prm = make(lp, np.float64, gram_tensor_cores=tc, At=At)
+    G = N(solver.sketch(T(d), 3))
+    solver.close()
+    A = At.T
+    W = hashing.gaussian_W(prm.seed, 3, n, 4 * m)
+    ref = A @ (d[:, None] * W)
+    absprod = np.abs(A) @ (d[:, None] * np.abs(W))
+    assert np.all(np.abs(G - ref) <= tol * absprod)
 
 
 def test_gaussian_normal_solve_matches_oracle():
