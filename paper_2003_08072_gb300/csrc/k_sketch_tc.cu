@@ -15,9 +15,12 @@
 // 2^24 and FP32 accumulation in the tensor core is exact.  The level sums of a chunk are folded
 // into double-float per thread.
 //
-// Layout.  Both digit arrays are written in the order the tensor core reads them: for each
-// block of 16 columns of A (kb) and each slice, the 8-row groups' core-matrix pairs (8 rows x
-// 16 bytes each) are contiguous, [kb][slice][row group][2][8][8].  The tensor core's M side is
+// Layout.  Both digit arrays are written tile by tile in the order the tensor core reads them:
+// W as [I][kb][slice][16 row groups][2][8][8], A D as [J][kb][slice][4 row groups][2][8][8]
+// (I, J the tiles of 128 sketch columns and of 32 rows of A, kb the blocks of 16 columns of A,
+// an 8-row group's two core matrices of 8 rows x 16 bytes), so the digits of one tile for
+// four consecutive k blocks are one contiguous range: a pipeline stage is two bulk copies
+// (32 KB of W, 36 KB of A D).  The tensor core's M side is
 // W (a tile of 128 sketch columns c, two slices), its N side A D (a tile of 32 rows i, nine
 // slices one after another), so one MMA of W slice t with the D slices s0 .. s1 writes the
 // level accumulators t + s0 .. t + s1, which lie side by side in tensor memory (level l at
@@ -49,12 +52,14 @@ constexpr int kKB = 16;                           // columns of A per stage (one
 constexpr int kSA = 9;                            // digit slices of A D
 constexpr int kSW = 2;                            // digit slices of W
 constexpr int kKC = 4096;                         // columns of A per exactly accumulated chunk
-constexpr int kNS = 8;                            // pipeline stages
+constexpr int kSK = 4;                            // k blocks per pipeline stage
+constexpr int kNS = 3;                            // pipeline stages
 constexpr int kWSlice = (kTM / 8) * tc::kCore;    // 4 KB: one slice of the W tile
 constexpr int kASlice = (kTI / 8) * tc::kCore;    // 1 KB: one slice of the A D tile
 constexpr int kWBytes = kSW * kWSlice;            // 8 KB
 constexpr int kABytes = kSA * kASlice;            // 9 KB
-constexpr int kStage = kWBytes + kABytes;         // 17 KB
+constexpr int kStageW = kSK * kWBytes;            // 32 KB: the stage's W digits
+constexpr int kStage = kStageW + kSK * kABytes;   // 68 KB: then its A D digits
 constexpr int kSmemBytes = kNS * kStage + 256;    // stages, mbarriers, TMEM address
 constexpr int kRowAlign = kTI;                    // rows of the A D digits: whole tiles
 
@@ -99,8 +104,9 @@ __global__ void __launch_bounds__(256) k_w_digits(uint64_t key, int64_t n, int w
       e0[e] = (float)d0;
       e1[e] = (float)(q - 64 * d0);
     }
-    const size_t base = (((size_t)kb * kSW * ngw + g) * 2 + hk) * 64 + r8 * 8;
-    const size_t sstep = (size_t)ngw * 128;   // elements of one slice of a k block
+    const size_t base =
+        ((((size_t)(g >> 4) * nkb + kb) * kSW * 16 + (g & 15)) * 2 + hk) * 64 + r8 * 8;
+    const size_t sstep = 16 * 128;   // elements of one slice of a tile's k block
     uint4 v0, v1;
     v0.x = pack_bf16(e0[0], e0[1]);
     v0.y = pack_bf16(e0[2], e0[3]);
@@ -191,8 +197,9 @@ __global__ void __launch_bounds__(256) k_ad_digits(const TA* __restrict__ A, int
       rh[e] = h * sc;   // exact scalings by a power of two
       rl[e] = l * sc;
     }
-    const size_t base = (((size_t)kb * kSA * ngm + g) * 2 + hk) * 64 + r8 * 8;
-    const size_t sstep = (size_t)ngm * 128;
+    const size_t base =
+        ((((size_t)(g >> 2) * nkb + kb) * kSA * 4 + (g & 3)) * 2 + hk) * 64 + r8 * 8;
+    const size_t sstep = 4 * 128;   // elements of one slice of a tile's k block
 #pragma unroll
     for (int s = 0; s < kSA; ++s) {
       float dg[8];
@@ -215,10 +222,9 @@ __global__ void __launch_bounds__(256) k_ad_digits(const TA* __restrict__ A, int
 
 // ---- the product ---------------------------------------------------------------------------
 struct SketchTcArgs {
-  const __nv_bfloat16* Wd;   // W digits, [kb][2][ngw][2][8][8]
-  const __nv_bfloat16* Dd;   // A D digits, [kb][9][ngm][2][8][8]
-  int ngw, ngm;              // 8-row groups of each
-  int64_t nkb;               // k blocks of 16 columns of A
+  const __nv_bfloat16* Wd;   // W digits, [I][kb][2][16][2][8][8]
+  const __nv_bfloat16* Dd;   // A D digits, [J][kb][9][4][2][8][8]
+  int64_t nkb;               // k blocks of 16 columns of A (a multiple of kSK)
   int NJ;                    // tiles along the rows of A (tile = I NJ + J)
   int ntile;
   int chunks_per_cta;        // chunks of kKC columns per CTA (blockIdx.y selects the range)
@@ -266,47 +272,40 @@ __global__ void __launch_bounds__(160, 1) k_sketch_tc(SketchTcArgs a) {
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sbase = smem_u32(smem);
-  const int nkb = (int)(kb1 - kb0);
+  const int nst = (int)((kb1 - kb0) / kSK);   // stages of this CTA (kb0, kb1 multiples of kSK)
+  constexpr int st_per_chunk = kb_per_chunk / kSK;
 
   if (warp == 4) {
-    // producer: block q of this CTA into stage q % kNS once the products of block q - kNS,
-    // the stage's last reader, are done
+    // producer: stage q (k blocks kb0 + kSK q ..) into buffer q % kNS once the products of
+    // stage q - kNS, the buffer's last reader, are done
     if (lane == 0) {
       const unsigned char* gW = reinterpret_cast<const unsigned char*>(a.Wd);
       const unsigned char* gD = reinterpret_cast<const unsigned char*>(a.Dd);
-      const size_t wslice = (size_t)a.ngw * tc::kCore, dslice = (size_t)a.ngm * tc::kCore;
-      const size_t w_off = (size_t)I * (kTM / 8) * tc::kCore;
-      const size_t d_off = (size_t)J * (kTI / 8) * tc::kCore;
-      for (int q = 0; q < nkb; ++q) {
+      for (int q = 0; q < nst; ++q) {
         const int st = q % kNS;
         if (q >= kNS && !mbar_wait_bounded(&empty[st], ((q / kNS) - 1) & 1, kWaitLimitNs)) {
           s_pfail = 1;
           break;
         }
         if (*(volatile int*)&s_gfail) break;
-        const size_t kb = (size_t)(kb0 + q);
+        const size_t kb = (size_t)(kb0 + (int64_t)q * kSK);
         unsigned char* dst = smem + st * kStage;
         mbar_arrive_expect_tx(&full[st], (unsigned)kStage);
-#pragma unroll
-        for (int t = 0; t < kSW; ++t)
-          bulk_g2s(dst + t * kWSlice, gW + (kb * kSW + t) * wslice + w_off, (unsigned)kWSlice,
-                   &full[st]);
-#pragma unroll
-        for (int s = 0; s < kSA; ++s)
-          bulk_g2s(dst + kWBytes + s * kASlice, gD + (kb * kSA + s) * dslice + d_off,
-                   (unsigned)kASlice, &full[st]);
+        bulk_g2s(dst, gW + ((size_t)I * a.nkb + kb) * kWBytes, (unsigned)kStageW, &full[st]);
+        bulk_g2s(dst + kStageW, gD + ((size_t)J * a.nkb + kb) * kABytes,
+                 (unsigned)(kStage - kStageW), &full[st]);
         s_issued = q + 1;
       }
     }
     __syncwarp();
   } else {
-    const uint64_t wdesc0 = tc::sdesc(sbase), ddesc0 = tc::sdesc(sbase + kWBytes);
+    const uint64_t desc0 = tc::sdesc(sbase);
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     float rh[kTI], rl[kTI];   // this thread's row of the partial tile, double-float
 #pragma unroll
     for (int c = 0; c < kTI; ++c) rh[c] = rl[c] = 0.f;
-    for (int c0 = 0; c0 < nkb; c0 += kb_per_chunk) {
-      const int c1 = min(nkb, c0 + kb_per_chunk);
+    for (int c0 = 0; c0 < nst; c0 += st_per_chunk) {
+      const int c1 = min(nst, c0 + st_per_chunk);
       if (tid == 0) {
         for (int q = c0; q < c1; ++q) {
           const int st = q % kNS;
@@ -315,20 +314,24 @@ __global__ void __launch_bounds__(160, 1) k_sketch_tc(SketchTcArgs a) {
             break;
           }
           tc::fence_after();
-          const uint32_t soff = (uint32_t)(st * kStage) >> 4;
-          const uint32_t first_acc = (q == c0) ? 0u : 1u;
-          const uint64_t w0 = wdesc0 + soff, w1 = w0 + (uint32_t)(kWSlice >> 4);
-          const uint64_t d0 = ddesc0 + soff, d8 = d0 + (uint32_t)((8 * kASlice) >> 4);
-          tc::mma(tmem, w0, d0, tc::idesc(kTM, 8 * kTI), first_acc);       // levels 0-7
-          tc::mma(tmem + 8 * kTI, w0, d8, tc::idesc(kTM, kTI), first_acc); // level 8
-          tc::mma(tmem + kTI, w1, d0, tc::idesc(kTM, 8 * kTI), 1u);        // levels 1-8
+#pragma unroll
+          for (int j = 0; j < kSK; ++j) {
+            const uint32_t first_acc = (q == c0 && j == 0) ? 0u : 1u;
+            const uint64_t w0 = desc0 + ((uint32_t)(st * kStage + j * kWBytes) >> 4);
+            const uint64_t w1 = w0 + (uint32_t)(kWSlice >> 4);
+            const uint64_t d0 = desc0 + ((uint32_t)(st * kStage + kStageW + j * kABytes) >> 4);
+            const uint64_t d8 = d0 + (uint32_t)((8 * kASlice) >> 4);
+            tc::mma(tmem, w0, d0, tc::idesc(kTM, 8 * kTI), first_acc);        // levels 0-7
+            tc::mma(tmem + 8 * kTI, w0, d8, tc::idesc(kTM, kTI), first_acc);  // level 8
+            tc::mma(tmem + kTI, w1, d0, tc::idesc(kTM, 8 * kTI), 1u);         // levels 1-8
+          }
           tc::commit(&empty[st]);
           s_consumed = q + 1;
         }
       }
       __syncwarp();
       fold_sync();
-      // all products of the chunk are done once the last block's empty barrier has fired
+      // all products of the chunk are done once the last stage's empty barrier has fired
       if (tid == 0 && !*(volatile int*)&s_gfail) {
         const int ql = c1 - 1;
         if (!mbar_wait_bounded(&empty[ql % kNS], (ql / kNS) & 1, kWaitLimitNs)) s_gfail = 1;
@@ -410,7 +413,7 @@ __global__ void k_sketch_tc_finish(const float2* __restrict__ part, int nsplit, 
 namespace {
 
 struct SketchTcShape {
-  int64_t nkb;        // k blocks of 16 columns of A
+  int64_t nkb;        // k blocks of 16 columns of A, padded to a multiple of kSK
   int ngw, ngm;       // 8-row groups of the W and A D digits
   int NI, NJ, ntile;  // tiles (128 sketch columns x 32 rows of A)
   int nchunks, split, per_cta;
@@ -424,7 +427,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // product is taken (fewer partial tiles to write and sum).
 SketchTcShape sketch_tc_shape(int m, int64_t n, int w, int num_sms) {
   SketchTcShape s{};
-  s.nkb = (n + kKB - 1) / kKB;
+  s.nkb = ((n + kKB - 1) / kKB + kSK - 1) / kSK * kSK;
   const int wp = (w + kTM - 1) / kTM * kTM, mp = (m + kRowAlign - 1) / kRowAlign * kRowAlign;
   s.ngw = wp / 8;
   s.ngm = mp / 8;
@@ -499,8 +502,6 @@ cudaError_t launch_sketch_tc(lp_dtype ta, const void* A, int64_t lda, int m, int
   SketchTcArgs a{};
   a.Wd = Wd;
   a.Dd = Dd;
-  a.ngw = s.ngw;
-  a.ngm = s.ngm;
   a.nkb = s.nkb;
   a.NJ = s.NJ;
   a.ntile = s.ntile;
