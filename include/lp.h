@@ -122,7 +122,9 @@ typedef struct {
                             waiting on per-tile counters (bounded waits: LP_ERR_TIMEOUT), so that only
                             the diagonal blocks' pivot chains are sequential; same arithmetic, bitwise
                             the same factor as 0: two launches per block step.  m above 8192 always
-                            takes the block-step launches (1) */
+                            takes the block-step launches, and so does a serving loop with
+                            max_live > 1 (its waiting CTAs would hold SMs from the other live
+                            instances) (1) */
 } lp_params;
 
 /* Per-solve report.  Filled on success and on LP_ERR_NOT_CONVERGED. */
