@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "bulk_util.cuh"
+#include "chol_tasks.h"
 #include "dev_util.cuh"
 
 namespace lpk {
@@ -649,12 +650,6 @@ __global__ void __launch_bounds__(256) k_ch_update(float* Ah, float* Al, float* 
 // same arithmetic, so both routes give bitwise the same L and X.  A lost pivot is flagged as
 // there; the sweep runs on with the replaced pivot (finite values) and the caller discards the
 // result.
-enum : uint32_t { CT_F = 0, CT_T = 1, CT_U = 2, CT_XS = 3, CT_XU = 4 };
-
-__host__ __device__ __forceinline__ uint32_t ct_pack(uint32_t kind, int i, int j, int k) {
-  return (kind << 27) | ((uint32_t)i << 18) | ((uint32_t)j << 9) | (uint32_t)k;
-}
-
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -867,36 +862,6 @@ __global__ void __launch_bounds__(256, 1) k_ch_dag(float* Ah, float* Al, float* 
     }
     dag_publish(cnt, val);
   }
-}
-
-// Task list of the one-launch sweep for nbk blocks (order above); returns the count, writes
-// the codes to out when out is not null.
-size_t chol_dag_tasks(int nbk, uint32_t* out) {
-  size_t n = 0;
-  auto put = [&](uint32_t kind, int i, int j, int k) {
-    if (out) out[n] = ct_pack(kind, i, j, k);
-    ++n;
-  };
-  auto step = [&](int k) {
-    for (int i = k + 2; i < nbk; ++i) put(CT_T, i, k, k);
-    for (int j = 0; j < k; ++j) put(CT_XS, k, j, k);
-    const bool ahead = k + 2 < nbk;   // the two tiles F(k + 2) reads
-    if (ahead) {
-      put(CT_U, k + 2, k + 1, k);
-      put(CT_U, k + 2, k + 2, k);
-    }
-    for (int j = k + 1; j < nbk; ++j)
-      for (int i = j; i < nbk; ++i) {
-        if (i == k + 1 && j == k + 1) continue;
-        if (ahead && i == k + 2 && (j == k + 1 || j == k + 2)) continue;
-        put(CT_U, i, j, k);
-      }
-    for (int i = k + 1; i < nbk; ++i)
-      for (int j = 0; j <= k; ++j) put(CT_XU, i, j, k);
-  };
-  put(CT_F, 0, 0, 0);
-  for (int k = 0; k < nbk; ++k) step(k);
-  return n;
 }
 
 // M = X^T X (lower tiles, summed over block rows q >= i) stored as DF pairs (Mh, Ml), mirrored.

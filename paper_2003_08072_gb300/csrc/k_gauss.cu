@@ -5,7 +5,7 @@
 //   h = SplitMix64(key ^ t),  j = h >> 50  (one of 2^14 equiprobable cells),
 //   W[i, b] = q_j / (2^8 sqrt(w)),  q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14)),
 // Phi the standard normal CDF.  The table q (|q_j| <= 1026) is computed once per process on the
-// host (gauss_grid) and kept in each context's device memory.  Every use of W (the sketch on
+// host (gauss_grid.h) and kept in each context's device memory.  Every use of W (the sketch on
 // either path and W u) reads the same table, so the sketch and the correction vector see the
 // same W and A S^-1 v = (A D W) u holds to the accuracy of G; the integer grid is what lets
 // the tensor-core sketch (k_sketch_tc.cu) form A D W exactly.
@@ -16,8 +16,6 @@
 // slice in chunks, generates the chunk's 8 columns of D W into shared memory as double-float
 // coefficients, accumulates in double-float and adds its partial sums into G with FP64
 // atomics; W u takes one thread per row of W with FP64 accumulation.
-#include <cmath>
-
 #include "dev_util.cuh"
 
 namespace lpk {
@@ -98,29 +96,6 @@ __global__ void k_apply_W_gauss(uint64_t key, int64_t n, int w, double rsw,
     double acc = 0.0;
     for (int b = 0; b < w; ++b) acc = fma((double)gauss_q(key, i, b, w, gq), u[b], acc);
     wu[i] = acc * rsw;
-  }
-}
-
-// q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14)): Phi^{-1} by bisection on Phi(z) = erfc(-z / sqrt 2)
-// / 2 over [-10, 0] to the resolution of FP64 (the cells below 1/2; the upper half by symmetry,
-// q_{N-1-j} = -q_j).  No table value lies within 1e-5 of a rounding tie, far above the error of
-// this evaluation, so any accurate evaluation of Phi^{-1} gives the same integers.
-void gauss_grid(int16_t* q) {
-  constexpr int N = 1 << kGaussBits;
-  for (int j = 0; j < N / 2; ++j) {
-    const double p = (j + 0.5) / N;
-    double lo = -10.0, hi = 0.0;
-    for (int it = 0; it < 80 && hi - lo > 0.0; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (0.5 * std::erfc(-mid * 0.70710678118654752440) < p)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    const long v = std::lrint(256.0 * 0.5 * (lo + hi));
-    q[j] = (int16_t)v;
-    q[N - 1 - j] = (int16_t)(-v);
   }
 }
 

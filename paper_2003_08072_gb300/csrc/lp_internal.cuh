@@ -11,6 +11,8 @@
 #include <vector>
 
 #include "../../include/lp.h"
+#include "chol_tasks.h"
+#include "gauss_grid.h"
 
 namespace lpk {
 
@@ -412,11 +414,11 @@ cudaError_t launch_add_shift(double* out, const double* Q, int mp, int m, double
 cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, int m, double eps,
                                 int* fl, cudaStream_t st, bool form_m = true);
 // The same Cholesky sweep as one launch of tile tasks in dependency order (k_factor.cu):
-// tasks from chol_dag_tasks (4 bytes each), sync = chol_dag_sync_words zeroed-per-launch words.
+// tasks from chol_dag_tasks (chol_tasks.h, 4 bytes each), sync = chol_dag_sync_words
+// zeroed-per-launch words.
 constexpr int kDagCtasPerSm = 2;    // CTAs per SM claiming tasks (126 registers a thread: 2 fit)
 constexpr int kDagMaxBlocks = 256;  // nbk above this keeps the block-step launches
 inline size_t chol_dag_sync_words(int nbk) { return 2 + 2 * (size_t)nbk * nbk; }
-size_t chol_dag_tasks(int nbk, uint32_t* out);
 cudaError_t launch_chol_dag(double* M, double* X, const double* Q0, int mp, int m, double eps,
                             const uint32_t* tasks, int ntasks, int* sync, int num_sms, int* fl,
                             cudaStream_t st, bool form_m = true);
@@ -556,8 +558,6 @@ cudaError_t launch_convert_dense(const void* src, lp_dtype sdt, bool rowmajor, i
                                  void* dst, lp_dtype ddt, int ldd, cudaStream_t st);
 // Gaussian sketch G = A D W (dense A, FP32 or FP64) and W u, W from (seed, k) and the quantile
 // table gq of 2^kGaussBits entries (k_gauss.cu: CUDA cores; k_sketch_tc.cu: tensor cores)
-constexpr int kGaussBits = 14;
-void gauss_grid(int16_t* q);   // host: the table, q_j = round(2^8 Phi^{-1}((j + 1/2) 2^-14))
 uint64_t gauss_iteration_key(uint64_t seed, int k);
 cudaError_t launch_sketch_gauss(lp_dtype ta, const void* A, int64_t lda, int m, int64_t n, int w,
                                 uint64_t seed, int k, const int16_t* gq, const double* d, double* G,
