@@ -121,8 +121,10 @@ typedef struct {
                             launch whose CTAs claim its 32 x 32 tile products in dependency order,
                             waiting on per-tile counters (bounded waits: LP_ERR_TIMEOUT), so that only
                             the diagonal blocks' pivot chains are sequential; same arithmetic, bitwise
-                            the same factor as 0: two launches per block step.  m above 8192 always
-                            takes the block-step launches, and so does a serving loop with
+                            the same factor as 0: two launches per block step.  m above 2048 always
+                            takes the block-step launches (there the sweep is bound by work, and
+                            the launch's task claims and waits cost more than the launches they
+                            save), and so does a serving loop with
                             max_live > 1 (its waiting CTAs would hold SMs from the other live
                             instances) (1) */
 } lp_params;

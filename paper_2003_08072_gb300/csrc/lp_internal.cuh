@@ -417,7 +417,10 @@ cudaError_t launch_chol_inverse(double* M, double* X, const double* Q0, int mp, 
 // tasks from chol_dag_tasks (chol_tasks.h, 4 bytes each), sync = chol_dag_sync_words
 // zeroed-per-launch words.
 constexpr int kDagCtasPerSm = 2;    // CTAs per SM claiming tasks (126 registers a thread: 2 fit)
-constexpr int kDagMaxBlocks = 256;  // nbk above this keeps the block-step launches
+constexpr int kDagMaxBlocks = 64;   // nbk above this keeps the block-step launches: there the
+                                    // sweep is work-bound and the tasks' claims, waits and
+                                    // fences cost more than the launches they save (measured:
+                                    // m = 1000 1.36 vs 1.57 ms, 2100 tie, 3000 16.2 vs 14.6 ms)
 inline size_t chol_dag_sync_words(int nbk) { return 2 + 2 * (size_t)nbk * nbk; }
 cudaError_t launch_chol_dag(double* M, double* X, const double* Q0, int mp, int m, double eps,
                             const uint32_t* tasks, int ntasks, int* sync, int num_sms, int* fl,
