@@ -384,7 +384,9 @@ __global__ void __launch_bounds__(160, 1) k_sketch_tc(SketchTcArgs a) {
 }
 
 // G (column-major, ldg x w) from the partial tiles: G_ic = 2^(e_i - 8) rsw sum over the splits,
-// zero on the padding rows m <= i < ldg.
+// zero on the padding rows m <= i < ldg.  The splits are summed in double-float on the FP32
+// pipes (each partial is a double-float pair already; FP64 adds run at a small fraction of
+// the FP32 rate on this GPU), then converted once.
 __global__ void k_sketch_tc_finish(const float2* __restrict__ part, int nsplit, int ntile, int NJ,
                                    const int* __restrict__ ex, int m, int ldg, int w, double rsw,
                                    double* __restrict__ G) {
@@ -396,13 +398,12 @@ __global__ void k_sketch_tc_finish(const float2* __restrict__ part, int nsplit, 
     if (i < m) {
       const int tile = (c / kTM) * NJ + i / kTI;
       const size_t off = ((size_t)tile * kTM + (c % kTM)) * kTI + (i % kTI);
-      double sh = 0.0, sl = 0.0;
+      float sh = 0.f, sl = 0.f;
       for (int sp = 0; sp < nsplit; ++sp) {
         const float2 p = part[(size_t)sp * ntile * kTM * kTI + off];
-        sh += (double)p.x;
-        sl += (double)p.y;
+        df_add(sh, sl, p.x, p.y);
       }
-      v = ldexp(sh + sl, ex[i] - 8) * rsw;
+      v = ldexp((double)sh + (double)sl, ex[i] - 8) * rsw;
     }
     G[idx] = v;
   }
@@ -475,7 +476,8 @@ cudaError_t launch_sketch_tc(lp_dtype ta, const void* A, int64_t lda, int m, int
   const int rows_p = s.ngm * 8;
   cudaError_t e = cudaMemsetAsync(ex, 0, (size_t)rows_p * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  const int ysplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, n / 4096));
+  // columns of A over blockIdx.y, ~512 per CTA, so that the row maxima spread over the GPU
+  const int ysplit = (int)std::max<int64_t>(1, std::min<int64_t>(4096, n / 512));
   const int64_t cap = (int64_t)num_sms * 16;
   const int64_t items_d = s.nkb * s.ngm * 16, items_w = s.nkb * s.ngw * 16;
   const unsigned grid_d = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, (items_d + 255) / 256));
