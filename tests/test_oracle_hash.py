@@ -98,24 +98,44 @@ def test_gaussian_W_moments_and_normality():
     assert stats.kstest(z[:200_000], "norm").pvalue > 1e-3
 
 
-def test_gaussian_grid_is_the_rounded_normal_quantile_table():
-    """q_j / 2^8 is the normal quantile of cell j's midpoint to within the 2^-9 rounding: the CDF
+def _grid_pin_holds(q):
+    """q / 2^8 is the normal quantile of cell j's midpoint to within the 2^-9 rounding: the CDF
     at q_j / 2^8 is (j + 1/2) 2^-14 within phi_max 2^-9 (plus FP64 rounding); the table is odd
-    (q_{N-1-j} = -q_j), non-decreasing, integer, and bounded by 1026."""
+    (q_{N-1-j} = -q_j), non-decreasing, integer; each grid value occurs for a run of
+    consecutive cells whose count matches the normal mass of its rounding interval to within
+    two cells."""
     from scipy import stats
 
-    q = hashing.gaussian_grid()
     N = q.size
-    assert N == 2**14 and np.array_equal(q, np.rint(q))
-    assert np.array_equal(q[::-1], -q) and np.all(np.diff(q) >= 0)
-    assert np.abs(q).max() == 1026
+    if N != 2**14 or not np.array_equal(q, np.rint(q)):
+        return False
+    if not (np.array_equal(q[::-1], -q) and np.all(np.diff(q) >= 0)):
+        return False
     mid = (np.arange(N) + 0.5) / N
-    assert np.abs(stats.norm.cdf(q / 256.0) - mid).max() <= 2.0**-9 / np.sqrt(2 * np.pi) + 1e-15
-    # the cells are equiprobable: each grid value occurs for a run of consecutive cells whose
-    # count matches the normal mass of its rounding interval to within two cells
+    if np.abs(stats.norm.cdf(q / 256.0) - mid).max() > 2.0**-9 / np.sqrt(2 * np.pi) + 1e-15:
+        return False
     vals, counts = np.unique(q, return_counts=True)
     mass = stats.norm.cdf((vals + 0.5) / 256) - stats.norm.cdf((vals - 0.5) / 256)
-    assert np.abs(counts - mass * N).max() <= 2.0
+    return bool(np.abs(counts - mass * N).max() <= 2.0)
+
+
+def test_gaussian_grid_is_the_rounded_normal_quantile_table():
+    q = hashing.gaussian_grid()
+    assert _grid_pin_holds(q)
+    assert np.abs(q).max() == 1026
+
+
+def test_gaussian_grid_pin_catches_planted_mistakes():
+    """Plausible slips in the table each fail the pin: the cell's left edge instead of its
+    midpoint, a grid of 2^-7 instead of 2^-8, truncation instead of rounding."""
+    from scipy import special
+
+    j = np.arange(2**14, dtype=np.float64)
+    left = np.rint(256.0 * special.ndtri(np.maximum(j, 0.5) / 2**14))
+    coarse = 2.0 * np.rint(128.0 * special.ndtri((j + 0.5) / 2**14))
+    trunc = np.trunc(256.0 * special.ndtri((j + 0.5) / 2**14))
+    for bad in (left, coarse, trunc):
+        assert not _grid_pin_holds(bad)
 
 
 def test_gaussian_W_is_a_function_of_seed_and_iteration_only():
