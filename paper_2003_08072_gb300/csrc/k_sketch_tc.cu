@@ -2,7 +2,7 @@
 // tensor cores, exact to the double-float accuracy of the entries of A D.
 //
 // The entries of W are integers over a common scale, W_kc = q_kc / (2^8 sqrt(w)) with
-// |q_kc| <= 1026 (the quantile grid of k_gauss.cu), so q splits exactly into two signed 6-bit
+// |q_kc| <= 1026 (the quantile grid of gauss_grid.h), so q splits exactly into two signed 6-bit
 // digits, q = 64 E_0 + E_1 (|E_0| <= 16, |E_1| <= 32).  Row i of A D is scaled by 2^-e_i
 // (max_k |A_ik d_k| < 2^e_i) and each scaled entry x = A_ik d_k 2^-e_i in (-1, 1), formed in
 // double-float, is written as nine signed 6-bit digits, x = sum_{s<9} D_s 2^(-6(s+1)) + r,
@@ -20,8 +20,8 @@
 // (I, J the tiles of 128 sketch columns and of 32 rows of A, kb the blocks of 16 columns of A,
 // an 8-row group's two core matrices of 8 rows x 16 bytes), so the digits of one tile for
 // four consecutive k blocks are one contiguous range: a pipeline stage is two bulk copies
-// (32 KB of W, 36 KB of A D).  The tensor core's M side is
-// W (a tile of 128 sketch columns c, two slices), its N side A D (a tile of 32 rows i, nine
+// (32 KB of W, 36 KB of A D).  The tensor core's M side is W (a tile of 128 sketch columns c,
+// two slices), its N side A D (a tile of 32 rows i, nine
 // slices one after another), so one MMA of W slice t with the D slices s0 .. s1 writes the
 // level accumulators t + s0 .. t + s1, which lie side by side in tensor memory (level l at
 // columns 32 l).  Per k block: E_0 x D_0..7 (levels 0-7, N = 256), E_0 x D_8 (level 8, N = 32),
@@ -29,7 +29,7 @@
 // other product accumulates.
 //
 // k_sketch_tc: one CTA per (128 x 32 tile of G^T, range of column chunks), 160 threads, one CTA
-// per SM (136 KB of shared memory, 512 tensor-memory columns).  Warp 4 (lane 0) issues the
+// per SM (204 KB of shared memory in 3 stages, 512 tensor-memory columns).  Warp 4 (lane 0) issues the
 // bulk copies of each stage (completing on its full mbarrier); warp 0 (lane 0) issues the
 // products and commits them to the stage's empty mbarrier; at the end of each chunk warps 0-3
 // read the accumulators back (thread t owns sketch column 128 I + t) and add them into
@@ -48,7 +48,7 @@ namespace {
 
 constexpr int kTM = 128;                          // sketch columns per tile (TMEM lanes)
 constexpr int kTI = 32;                           // rows of A per tile
-constexpr int kKB = 16;                           // columns of A per stage (one MMA K step)
+constexpr int kKB = 16;                           // columns of A per k block (one MMA K step)
 constexpr int kSA = 9;                            // digit slices of A D
 constexpr int kSW = 2;                            // digit slices of W
 constexpr int kKC = 4096;                         // columns of A per exactly accumulated chunk
