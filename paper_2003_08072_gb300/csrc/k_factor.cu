@@ -9,6 +9,8 @@
 //      row-major mp x mp matrix (identity on the padding).
 //   2. Q^{-1} = L^{-T} L^{-1} from a blocked Cholesky factor Q = L L^T (Q is symmetric positive
 //      definite when rank(A D W) = m, Lemma 4.1); a lost pivot flags a numerically singular Q.
+//      The sweep runs either as two launches per block step or as one launch of tile tasks in
+//      dependency order (k_ch_dag); both give bitwise the same L and L^{-1}.
 #include <algorithm>
 
 #include "bulk_util.cuh"
