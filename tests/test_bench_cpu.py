@@ -91,3 +91,4 @@ def test_traffic_figure_matches_its_profile_summary():
     assert bench.NCU_TRAFFIC["source_sha1"] in text
     mb = float(re.search(r"traffic per launch \| \*\*([0-9.]+) MB\*\*", text).group(1))
     assert abs(bench.NCU_TRAFFIC["bytes_per_launch"] - mb * 1e6) <= 0.01e6
+
