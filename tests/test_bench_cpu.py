@@ -92,3 +92,15 @@ def test_traffic_figure_matches_its_profile_summary():
     mb = float(re.search(r"traffic per launch \| \*\*([0-9.]+) MB\*\*", text).group(1))
     assert abs(bench.NCU_TRAFFIC["bytes_per_launch"] - mb * 1e6) <= 0.01e6
 
+
+
+def test_stored_oracle_runs_are_found(monkeypatch):
+    """The bench's dense and badly scaled workloads at their default sizes find the oracle's
+    own stored run of the same instance (tests/golden/make_oracle_run.py)."""
+    import bench
+
+    for wl in ("dense", "scaled"):
+        rec = bench.oracle_run_record(_args(monkeypatch, "--workload", wl))
+        assert rec is not None and rec["converged"] and rec["ipm_iters"] > 0, wl
+        assert wl in rec["command"]
+    assert bench.oracle_run_record(_args(monkeypatch, "--workload", "sparse")) is None
