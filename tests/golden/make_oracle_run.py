@@ -9,6 +9,7 @@ very instance the GPU solves.  Calls only oracle/ and synth/.
 
     python tests/golden/make_oracle_run.py dense 1000 200000 f32 4
     python tests/golden/make_oracle_run.py scaled 2000 500000 f32 4   (columns scaled by 10^U(-3,3))
+    python tests/golden/make_oracle_run.py sparse 5000 2000000 f32 4  (CSR, 8 nonzeros per column)
 """
 import json
 import os
@@ -26,15 +27,23 @@ from oracle import iipm  # noqa: E402
 
 def main():
     kind, m, n, dt, s = sys.argv[1], int(sys.argv[2]), int(sys.argv[3]), sys.argv[4], int(sys.argv[5])
-    assert kind in ("dense", "scaled")
-    lp = synth.dense_lp(0, m, n, dtype=np.float32 if dt == "f32" else np.float64,
-                        col_scale=(-3, 3) if kind == "scaled" else None)
-    A = np.ascontiguousarray(lp.A, dtype=np.float64)
+    assert kind in ("dense", "scaled", "sparse")
+    if kind == "sparse":
+        lp = synth.sparse_lp(0, m, n, nnz_per_col=8)
+        A = lp.to_scipy().astype(np.float64)
+    else:
+        lp = synth.dense_lp(0, m, n, dtype=np.float32 if dt == "f32" else np.float64,
+                            col_scale=(-3, 3) if kind == "scaled" else None)
+        A = np.ascontiguousarray(lp.A, dtype=np.float64)
     t0 = time.perf_counter()
     r = iipm.ipm_solve(A, lp.b, lp.c, iipm.Params(sketch_s=s))
     secs = time.perf_counter() - t0
-    desc = "dense Gaussian LP" + (" with column scales 10^U(-3,3)" if kind == "scaled" else "")
-    out = {"workload": f"{desc} m={m} n={n} A {dt.upper()} seed 0 (synth.dense_lp)",
+    if kind == "sparse":
+        desc, gen = "sparse LP, 8 nonzeros per column, CSR", "synth.sparse_lp"
+    else:
+        desc = "dense Gaussian LP" + (" with column scales 10^U(-3,3)" if kind == "scaled" else "")
+        gen = "synth.dense_lp"
+    out = {"workload": f"{desc} m={m} n={n} A {dt.upper()} seed 0 ({gen})",
            "sketch_s": s, "ipm_iters": int(r.iters), "cg_total": int(r.cg_total),
            "objective": float(r.obj), "kkt": float(r.kkt), "converged": bool(r.converged),
            "seconds": secs, "cores": os.cpu_count(),
