@@ -305,7 +305,7 @@ def sample_lp(args):
 def oracle_run_record(args):
     """The oracle's own end-to-end run of the full workload instance, stored by
     tests/golden/make_oracle_run.py (IPM iterations, CG products, objective), or None."""
-    if args.workload not in ("dense", "scaled") or args.sketch != "sparse":
+    if args.workload not in ("dense", "scaled", "sparse") or args.sketch != "sparse":
         return None
     path = os.path.join(ROOT, "tests", "golden", f"oracle_run_{args.workload}_m{args.m}_n{args.n}"
                         f"_{args.dtype}_s{args.sketch_s}.json")

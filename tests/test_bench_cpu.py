@@ -95,12 +95,12 @@ def test_traffic_figure_matches_its_profile_summary():
 
 
 def test_stored_oracle_runs_are_found(monkeypatch):
-    """The bench's dense and badly scaled workloads at their default sizes find the oracle's
-    own stored run of the same instance (tests/golden/make_oracle_run.py)."""
+    """The bench's dense, badly scaled and sparse workloads at their default sizes find the
+    oracle's own stored run of the same instance (tests/golden/make_oracle_run.py)."""
     import bench
 
-    for wl in ("dense", "scaled"):
+    for wl in ("dense", "scaled", "sparse"):
         rec = bench.oracle_run_record(_args(monkeypatch, "--workload", wl))
         assert rec is not None and rec["converged"] and rec["ipm_iters"] > 0, wl
         assert wl in rec["command"]
-    assert bench.oracle_run_record(_args(monkeypatch, "--workload", "sparse")) is None
+    assert bench.oracle_run_record(_args(monkeypatch, "--workload", "serving")) is None
